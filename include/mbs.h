@@ -1,0 +1,246 @@
+/*
+ * mbs.h - C ABI of the GB300 multibody scattering library.
+ *
+ * The library solves the multibody sound-soft scattering problem with local
+ * MFS scattering matrices (Cai, Bagge, Martinsson, "A stable and fast method
+ * for solving multibody scattering problems via the method of fundamental
+ * solutions"):
+ *
+ *     (I + S G_hat) q_hat = S v_hat                        (Sec. 2.2, eq. mbody2)
+ *
+ * where S = diag(S_tau) holds one k_tau x k_tau scattering matrix per body
+ * (Sec. 4.5, eq. scattering-matrix), G_hat(i, j) = phi_kappa(x_hat_i - x_hat_j)
+ * between skeleton points of different bodies (Sec. 1, eq. Gmtx-entries) and
+ * phi_kappa is (i/4) H0^(1)(kappa r) in 2D, exp(i kappa r) / (4 pi r) in 3D
+ * (Sec. 3.1, eq. FundamentalSol).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex arrays are interleaved (re, im) doubles.  A block of nrhs
+ *    vectors of length L is column-major: element (i, r) is at
+ *    [2 * (r * L + i)] (re) and [2 * (r * L + i) + 1] (im).
+ *  - Point sets are structure-of-arrays: coordinate c of point i of a set of
+ *    L points is at [c * L + i].
+ *  - Every array argument may be a host pointer or a CUDA device pointer of
+ *    the current device; the library tells them apart with
+ *    cudaPointerGetAttributes.  Host buffers are copied in and out inside the
+ *    call; device buffers are used in place on the context's stream, and the
+ *    call returns after the stream has finished with them.
+ *  - The caller keeps ownership of every buffer it passes; the library copies
+ *    what it needs.  The library owns the context and all device memory it
+ *    allocates; mbs_destroy releases it.
+ *  - Every call returns an mbs_status; no exception crosses the ABI.  On an
+ *    error the context keeps its previous valid state and mbs_last_error()
+ *    describes the failure.  Calls on one context are serialised by a
+ *    per-context mutex; different contexts may be used from different
+ *    threads.
+ */
+#ifndef MBS_H
+#define MBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mbs_status {
+    MBS_OK = 0,
+    MBS_ERR_ARG = 1,          /* invalid argument: size, null pointer, NaN/Inf input */
+    MBS_ERR_GEOMETRY = 2,     /* a body reaches inside another body's proxy surface */
+    MBS_ERR_NOMEM = 3,        /* device allocation failed or the HBM budget is exceeded */
+    MBS_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    MBS_ERR_NOCONV = 5,       /* the solve hit max_iter / max_sweeps; q_hat holds the best iterate */
+    MBS_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out */
+    MBS_ERR_NEAR_TARGET = 7,  /* an evaluation target lies inside a proxy surface */
+    MBS_ERR_STATE = 8,        /* call out of order (e.g. solve before build) */
+    MBS_ERR_UNSUPPORTED = 9   /* option combination not implemented */
+} mbs_status;
+
+enum {
+    MBS_PREC_FP64 = 0,   /* every step in FP64 */
+    MBS_PREC_MIXED = 1,  /* FP32 G_hat/S/Krylov inside FP64 iterative refinement */
+    MBS_PREC_FP32 = 2    /* apply calls only: the FP32 operator itself */
+};
+
+typedef struct mbs_options {
+    int precision;       /* MBS_PREC_FP64 or MBS_PREC_MIXED (solve); apply calls accept FP32 too */
+    double tol;          /* stop when ||b - A q||_2 / ||b||_2 <= tol for every RHS (FP64 residual) */
+    double inner_tol;    /* mixed precision: relative residual target of each FP32 inner solve */
+    int restart;         /* GMRES restart length (Krylov vectors kept per RHS) */
+    int max_iter;        /* cap on Arnoldi steps summed over the whole solve */
+    int max_sweeps;      /* mixed precision: cap on refinement sweeps */
+    double ls_rcond;     /* relative truncation of the least-squares solves in the S build */
+    void* stream;        /* cudaStream_t to run on, or NULL for a stream the context creates */
+    size_t hbm_budget;   /* bytes of device memory the context may hold (0 = no cap) */
+    int tile_override;   /* 0 = tuned launch shape; >0 forces the source-split count of G_hat */
+} mbs_options;
+
+typedef struct mbs_shape {
+    int m;               /* collocation points on Gamma (Sec. 3.1) */
+    int n;               /* MFS sources inside Gamma, n < m (Sec. 3.1) */
+    int p;               /* proxy points on Psi (Sec. 4.2) */
+    const double* x;     /* m collocation points, local frame, SoA (dim * m) */
+    const double* y;     /* n MFS sources, SoA (dim * n) */
+    const double* z;     /* p proxy points, SoA (dim * p) */
+    int k;               /* fixed skeleton count (k <= min(m, p)), or 0: stop the pivoted QR at eps */
+    double eps;          /* relative stopping tolerance of the pivoted QR when k == 0 */
+    double proxy_radius; /* radius of the proxy circle/sphere about the local origin */
+} mbs_shape;
+
+typedef struct mbs_body {
+    int shape;           /* index into the shapes array */
+    double c[3];         /* centre (world frame); c[2] ignored in 2D */
+    double R[9];         /* row-major rotation, x_world = c + R x_local; 2D uses R[0], R[1], R[3], R[4] */
+} mbs_body;
+
+typedef struct mbs_solve_info {
+    int inner_iterations; /* Arnoldi steps, summed over RHS batches and sweeps */
+    int sweeps;           /* refinement sweeps (mixed) or restart cycles (FP64) */
+    int matvecs_fp32;     /* FP32 operator applications (each covers all RHS) */
+    int matvecs_fp64;     /* FP64 operator applications (each covers all RHS) */
+    int converged;        /* 1 if every RHS reached tol */
+    double rel_residual;  /* max over RHS of the final FP64 relative residual */
+    double seconds;       /* wall time of the call */
+} mbs_solve_info;
+
+typedef struct mbs_ctx mbs_ctx;
+
+/* Fill *opt with defaults: FP64, tol 1e-11, inner_tol 1e-6, restart 60,
+ * max_iter 20000, max_sweeps 8, ls_rcond 1e-14, stream NULL, no budget. */
+void mbs_default_options(mbs_options* opt);
+
+/* Create a context for dimension dim (2 or 3) and wavenumber kappa > 0
+ * (Sec. 2.1, eq. BVP).  opt may be NULL for defaults.  Errors: MBS_ERR_ARG,
+ * MBS_ERR_CUDA. */
+mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void mbs_destroy(mbs_ctx* ctx);
+
+/* Replace the options of a live context (precision, tolerances, stream...). */
+mbs_status mbs_set_options(mbs_ctx* ctx, const mbs_options* opt);
+
+/* Text of the last error on this context ("" if none); owned by the context. */
+const char* mbs_last_error(const mbs_ctx* ctx);
+
+/*
+ * build_scattering_matrices(bodies, kappa)  (Sec. 4.2-4.5).
+ * For every shape used by a body: B(i,j) = phi(z_i - x_j) (p x m), its column-
+ * pivoted QR halted at k (or eps) gives the skeleton I_hat and Z* with
+ * B ~ B(:, I_hat) Z* (eq. B_fac); A(i,j) = phi(x_i - y_j) (m x n) and
+ * D(i,j) = phi(z_i - y_j) (p x n) give the local solve A^+ and the translation
+ * C with B C = D; S = Z* C A^+ U with U = (Z*)^T (eq. scattering-matrix).
+ * Bodies are rigid placements of shapes (S is reused per shape, Sec. 5.1
+ * Example 4).  All of it runs on the device in FP64.
+ * Errors: MBS_ERR_ARG (n >= m, k > min(m,p), NaN, bad shape index),
+ * MBS_ERR_GEOMETRY (some point of a body inside another body's proxy radius),
+ * MBS_ERR_NOMEM, MBS_ERR_CUDA.
+ */
+mbs_status mbs_build_scattering_matrices(mbs_ctx* ctx, int nshapes, const mbs_shape* shapes,
+                                          int nbodies, const mbs_body* bodies);
+
+/* Layout of q_hat: *N = sum_tau k_tau; body_offsets (nbodies + 1 entries,
+ * nullable) gives the first skeleton of each body; skel_xyz (dim * N, SoA,
+ * nullable) the world coordinates x_hat.  Outputs are caller-allocated. */
+mbs_status mbs_get_layout(mbs_ctx* ctx, int64_t* N, int64_t* body_offsets, double* skel_xyz);
+
+/* Scattering data of one shape as built: *k, skel (k indices into the
+ * shape's collocation points, nullable), S (k x k complex, column-major,
+ * nullable), eps_achieved (nullable: largest remaining column norm of B over
+ * its largest initial column norm when the QR stopped). */
+mbs_status mbs_get_shape(mbs_ctx* ctx, int shape, int* k, int* skel, double* S,
+                         double* eps_achieved);
+
+/*
+ * Right-hand side b = S v_hat, evaluated as Z* C A^+ v from the boundary data
+ * v = -u_inc at all m collocation points of each body (Sec. 4.5, last
+ * display).  v: (sum_tau m_tau) x nrhs complex, bodies in order; b: N x nrhs.
+ */
+mbs_status mbs_rhs(mbs_ctx* ctx, int nrhs, const double* v, double* b);
+
+/* apply_operator(q_hat): y = q_hat + S G_hat q_hat (eq. mbody2), N x nrhs,
+ * in the context's precision (FP32 evaluates G_hat and S in single precision
+ * with FP32 accumulation; inputs and outputs stay FP64). */
+mbs_status mbs_apply_operator(mbs_ctx* ctx, int nrhs, const double* qhat, double* y);
+
+/* y = G_hat q (N x nrhs), precision MBS_PREC_FP64 or MBS_PREC_FP32 (Sec. 2.2). */
+mbs_status mbs_apply_G(mbs_ctx* ctx, int precision, int nrhs, const double* q, double* y);
+
+/*
+ * solve(v_hat) -> q_hat: GMRES on (I + S G_hat) q_hat = b (Sec. 2.4), in FP64
+ * or as FP32 GMRES inside FP64 iterative refinement (precision option).
+ * b: N x nrhs.  qhat: on entry the initial guess (all zeros allowed); on
+ * exit the solution (the best iterate on MBS_ERR_NOCONV).  info nullable.
+ */
+mbs_status mbs_solve(mbs_ctx* ctx, int nrhs, const double* b, double* qhat, mbs_solve_info* info);
+
+/*
+ * evaluate_field(points): scattered field u(t) = sum_i phi(t - x_hat_i) q_hat_i
+ * (Sec. 4.1, eq. out_skel) at M targets (SoA dim * M), in FP64.  Every target
+ * must lie on or outside every proxy surface; otherwise MBS_ERR_NEAR_TARGET
+ * (near-field reconstruction, Sec. 4.6, is not provided).  u: M x nrhs.
+ */
+mbs_status mbs_evaluate_field(mbs_ctx* ctx, int nrhs, int64_t M, const double* pts,
+                              const double* qhat, double* u);
+
+/*
+ * Test hook: replace the built scattering data of one shape with externally
+ * computed data (e.g. the CPU reference), isolating the global solve.
+ * skel: k indices into the shape's collocation points; S: k x k complex;
+ * W: k x m complex (b_tau = W v_tau), or NULL to keep the built right-hand
+ * side operator.  Skeleton coordinates are recomputed for every body.
+ */
+mbs_status mbs_inject_scattering(mbs_ctx* ctx, int shape, int k, const int* skel,
+                                 const double* S, const double* W);
+
+/* Measure device peaks with short microbenchmarks: out[0] FP32 FMA TFLOP/s,
+ * out[1] FP64 FMA TFLOP/s, out[2] MUFU (sin+cos+rsqrt) Tops/s, out[3] SM
+ * count, out[4] SM clock kHz.  Runs on the current device. */
+mbs_status mbs_measure_peaks(double* out);
+
+/* ---- serving: continuous batching of independent solves (one GPU) ---- */
+typedef struct mbs_server mbs_server;
+
+typedef struct mbs_request {
+    int dim;
+    double kappa;
+    int nshapes;
+    const mbs_shape* shapes;
+    int nbodies;
+    const mbs_body* bodies;
+    int nrhs;
+    const double* v;      /* (sum m) x nrhs boundary data, host memory, copied at submit */
+    double tol;           /* relative residual target (mixed precision solve) */
+} mbs_request;
+
+typedef struct mbs_request_result {
+    int done;             /* 0 queued/running, 1 finished, -1 failed */
+    mbs_status status;
+    int64_t N;
+    double rel_residual;
+    int inner_iterations;
+    double t_submit, t_start, t_end;   /* seconds on the server's clock */
+} mbs_request_result;
+
+/* Create a server with max_active concurrent solves and an HBM budget in
+ * bytes (0 = 90 % of free device memory).  Requests are admitted in arrival
+ * order when their estimated footprint fits and a slot is free; admitted
+ * solves advance in an interleaved way on separate CUDA streams. */
+mbs_status mbs_serve_create(int max_active, size_t hbm_budget, mbs_server** out);
+/* Queue a request; *id receives its handle.  Inputs are copied. */
+mbs_status mbs_serve_submit(mbs_server* srv, const mbs_request* req, int64_t* id);
+/* Poll (non-blocking) the state of a request; if it is done and qhat is not
+ * NULL, copy its solution (N x nrhs complex, host memory) there. */
+mbs_status mbs_serve_poll(mbs_server* srv, int64_t id, mbs_request_result* res, double* qhat);
+/* Block until every submitted request has finished. */
+mbs_status mbs_serve_drain(mbs_server* srv);
+/* Stop the worker thread and free everything. */
+void mbs_serve_destroy(mbs_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBS_H */

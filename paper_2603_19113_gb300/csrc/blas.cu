@@ -1,0 +1,355 @@
+// Block-diagonal S application and the multi-RHS Krylov vector kernels.
+//
+// z_tau = x_tau + S_tau y_tau for every body tau (the "I +" and "S" of
+// eq. mbody2, Sec. 2.2), with S_tau k_tau x k_tau column-major and shared
+// between bodies of one shape.  Vectors are stored [nrhs][N].
+#include "common.cuh"
+
+namespace {
+
+template <typename V>
+struct Acc;
+template <>
+struct Acc<float2> {
+    using T = float;
+};
+template <>
+struct Acc<double2> {
+    using T = double;
+};
+
+template <typename V>
+__device__ __forceinline__ const V* sptr(const SBlocks& B, int t);
+template <>
+__device__ __forceinline__ const float2* sptr<float2>(const SBlocks& B, int t) {
+    return B.S32[t];
+}
+template <>
+__device__ __forceinline__ const double2* sptr<double2>(const SBlocks& B, int t) {
+    return B.S64[t];
+}
+
+constexpr int SA_RC = 8;  // right-hand sides per pass
+
+// One CTA per body; y_tau staged in shared memory SA_RC columns at a time.
+template <typename V>
+__global__ void __launch_bounds__(256) sapply_kernel(const SBlocks B, const int64_t N,
+                                                     const int nrhs, const V* __restrict__ x,
+                                                     const V* __restrict__ y, V* __restrict__ z) {
+    using T = typename Acc<V>::T;
+    extern __shared__ unsigned char smem_raw[];
+    V* s_y = reinterpret_cast<V*>(smem_raw);
+    const int tau = blockIdx.x;
+    const int k = B.k[tau];
+    const int64_t o = B.off[tau];
+    const V* __restrict__ S = sptr<V>(B, tau);
+    for (int rc = 0; rc < nrhs; rc += SA_RC) {
+        const int nr = min(SA_RC, nrhs - rc);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * nr; idx += blockDim.x) {
+            const int r = idx / k, i = idx - r * k;
+            s_y[r * k + i] = y[(int64_t)(rc + r) * N + o + i];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            T ar[SA_RC], ai[SA_RC];
+#pragma unroll
+            for (int r = 0; r < SA_RC; ++r) ar[r] = ai[r] = T(0);
+            for (int j = 0; j < k; ++j) {
+                const V s = S[(int64_t)j * k + i];
+#pragma unroll
+                for (int r = 0; r < SA_RC; ++r) {
+                    if (r < nr) {
+                        const V v = s_y[r * k + j];
+                        ar[r] = fma(s.x, v.x, fma(-s.y, v.y, ar[r]));
+                        ai[r] = fma(s.x, v.y, fma(s.y, v.x, ai[r]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < SA_RC; ++r) {
+                if (r < nr) {
+                    const int64_t g = (int64_t)(rc + r) * N + o + i;
+                    V out;
+                    const V xv = x[g];
+                    out.x = xv.x + ar[r];
+                    out.y = xv.y + ai[r];
+                    z[g] = out;
+                }
+            }
+        }
+    }
+}
+
+// partial[(i*nrhs + r) * nblk + blk] = sum over the block's slice of conj(basis_i,r) . w_r
+template <typename V>
+__global__ void __launch_bounds__(256) dots_kernel(const V* __restrict__ basis, const int nvec,
+                                                   const V* __restrict__ w, const int64_t N,
+                                                   const int nrhs, double2* __restrict__ partial,
+                                                   const int nblk) {
+    const int ir = blockIdx.y;  // i * nrhs + r
+    const int r = ir % nrhs;
+    const V* __restrict__ vb = basis + (int64_t)ir * N;
+    const V* __restrict__ wr = w + (int64_t)r * N;
+    double sx = 0.0, sy = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const V a = vb[n], b = wr[n];
+        sx += (double)a.x * b.x + (double)a.y * b.y;
+        sy += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    __shared__ double rx[256], ry[256];
+    rx[threadIdx.x] = sx;
+    ry[threadIdx.x] = sy;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            rx[threadIdx.x] += rx[threadIdx.x + s];
+            ry[threadIdx.x] += ry[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)ir * nblk + blockIdx.x] = make_double2(rx[0], ry[0]);
+}
+
+__global__ void dots_finish_kernel(const double2* __restrict__ partial, int count, int nblk,
+                                   double2* __restrict__ out) {
+    const int ir = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ir >= count) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(int64_t)ir * nblk + b]);
+    out[ir] = s;
+}
+
+// w_r += sign * sum_i basis_{i,r} h[i * nrhs + r]
+template <typename V>
+__global__ void __launch_bounds__(256) update_kernel(const V* __restrict__ basis, const int nvec,
+                                                     const double2* __restrict__ h,
+                                                     V* __restrict__ w, const int64_t N,
+                                                     const int nrhs, const double sign) {
+    using T = typename Acc<V>::T;
+    const int r = blockIdx.y;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        double ax = 0.0, ay = 0.0;
+        for (int i = 0; i < nvec; ++i) {
+            const V v = basis[((int64_t)i * nrhs + r) * N + n];
+            const double2 c = h[i * nrhs + r];
+            ax += (double)v.x * c.x - (double)v.y * c.y;
+            ay += (double)v.x * c.y + (double)v.y * c.x;
+        }
+        V o = w[(int64_t)r * N + n];
+        o.x = (T)((double)o.x + sign * ax);
+        o.y = (T)((double)o.y + sign * ay);
+        w[(int64_t)r * N + n] = o;
+    }
+}
+
+template <typename V>
+__global__ void scale_kernel(const V* __restrict__ w, const double* __restrict__ inv,
+                             V* __restrict__ out, const int64_t N, const int nrhs) {
+    using T = typename Acc<V>::T;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * nrhs) return;
+    const T s = (T)inv[i / N];
+    V v = w[i];
+    v.x *= s;
+    v.y *= s;
+    out[i] = v;
+}
+
+__global__ void norms_kernel(const double2* __restrict__ x, const int64_t N, const int nrhs,
+                             double* __restrict__ partial, const int nblk) {
+    const int r = blockIdx.y;
+    double s = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (int64_t)gridDim.x * blockDim.x)
+        s += cabs2(x[(int64_t)r * N + n]);
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)r * nblk + blockIdx.x] = red[0];
+}
+
+__global__ void norms_finish_kernel(const double* __restrict__ partial, int nrhs, int nblk,
+                                    double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)r * nblk + b];
+    out[r] = sqrt(s);
+}
+
+__global__ void f64_to_f32_scaled_kernel(const double2* __restrict__ x,
+                                         const double* __restrict__ scale,
+                                         float2* __restrict__ y, int64_t N, int nrhs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * nrhs) return;
+    const double s = scale[i / N];
+    y[i] = make_float2((float)(x[i].x * s), (float)(x[i].y * s));
+}
+
+__global__ void axpy_f32_into_f64_kernel(const float2* __restrict__ d,
+                                         const double* __restrict__ scale,
+                                         double2* __restrict__ x, int64_t N, int nrhs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * nrhs) return;
+    const double s = scale[i / N];
+    x[i].x += s * (double)d[i].x;
+    x[i].y += s * (double)d[i].y;
+}
+
+__global__ void sub64_kernel(const double2* __restrict__ b, const double2* __restrict__ ax,
+                             double2* __restrict__ r, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    r[i] = csub(b[i], ax[i]);
+}
+
+template <typename V>
+__global__ void sub_kernel(const V* __restrict__ b, const V* __restrict__ ax, V* __restrict__ r,
+                           int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V o;
+    o.x = b[i].x - ax[i].x;
+    o.y = b[i].y - ax[i].y;
+    r[i] = o;
+}
+
+__global__ void f32_to_f64_kernel(const float2* __restrict__ a, double2* __restrict__ b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_double2(a[i].x, a[i].y);
+}
+
+__global__ void f64_to_f32_kernel(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int mbs_num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+void launch_sapply_f32(const SBlocks& B, int64_t N, int nrhs, const float2* x, const float2* y,
+                       float2* z, int kmax, cudaStream_t st) {
+    if (B.T == 0 || nrhs == 0) return;
+    const size_t sm = (size_t)kmax * SA_RC * sizeof(float2);
+    if (sm > 48 * 1024)
+        MBS_CUDA_TRY(cudaFuncSetAttribute(sapply_kernel<float2>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    sapply_kernel<float2><<<B.T, 256, sm, st>>>(B, N, nrhs, x, y, z);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_sapply_f64(const SBlocks& B, int64_t N, int nrhs, const double2* x, const double2* y,
+                       double2* z, int kmax, cudaStream_t st) {
+    if (B.T == 0 || nrhs == 0) return;
+    const size_t sm = (size_t)kmax * SA_RC * sizeof(double2);
+    if (sm > 48 * 1024)
+        MBS_CUDA_TRY(cudaFuncSetAttribute(sapply_kernel<double2>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    sapply_kernel<double2><<<B.T, 256, sm, st>>>(B, N, nrhs, x, y, z);
+    MBS_CHECK_LAUNCH();
+}
+
+template <typename V>
+void launch_dots(const V* basis, int nvec, const V* w, int64_t N, int nrhs, double2* out,
+                 double2* scratch, int nblk, cudaStream_t st) {
+    if (nvec == 0) return;
+    dim3 g((unsigned)nblk, (unsigned)(nvec * nrhs));
+    dots_kernel<V><<<g, 256, 0, st>>>(basis, nvec, w, N, nrhs, scratch, nblk);
+    MBS_CHECK_LAUNCH();
+    dots_finish_kernel<<<nblocks(nvec * nrhs, 128), 128, 0, st>>>(scratch, nvec * nrhs, nblk, out);
+    MBS_CHECK_LAUNCH();
+}
+
+template <typename V>
+void launch_update(const V* basis, int nvec, const double2* h, V* w, int64_t N, int nrhs,
+                   double sign, cudaStream_t st) {
+    if (nvec == 0) return;
+    const unsigned gx = (unsigned)std::min<int64_t>((N + 255) / 256, 4 * mbs_num_sms());
+    dim3 g(gx, (unsigned)nrhs);
+    update_kernel<V><<<g, 256, 0, st>>>(basis, nvec, h, w, N, nrhs, sign);
+    MBS_CHECK_LAUNCH();
+}
+
+template <typename V>
+void launch_scale(V* w, const double* inv, V* out, int64_t N, int nrhs, cudaStream_t st) {
+    scale_kernel<V><<<nblocks(N * nrhs), 256, 0, st>>>(w, inv, out, N, nrhs);
+    MBS_CHECK_LAUNCH();
+}
+
+template void launch_dots<float2>(const float2*, int, const float2*, int64_t, int, double2*,
+                                  double2*, int, cudaStream_t);
+template void launch_dots<double2>(const double2*, int, const double2*, int64_t, int, double2*,
+                                   double2*, int, cudaStream_t);
+template void launch_update<float2>(const float2*, int, const double2*, float2*, int64_t, int,
+                                    double, cudaStream_t);
+template void launch_update<double2>(const double2*, int, const double2*, double2*, int64_t, int,
+                                     double, cudaStream_t);
+template void launch_scale<float2>(float2*, const double*, float2*, int64_t, int, cudaStream_t);
+template void launch_scale<double2>(double2*, const double*, double2*, int64_t, int, cudaStream_t);
+
+void launch_norms64(const double2* x, int64_t N, int nrhs, double* out, double* scratch, int nblk,
+                    cudaStream_t st) {
+    dim3 g((unsigned)nblk, (unsigned)nrhs);
+    norms_kernel<<<g, 256, 0, st>>>(x, N, nrhs, scratch, nblk);
+    MBS_CHECK_LAUNCH();
+    norms_finish_kernel<<<nblocks(nrhs, 64), 64, 0, st>>>(scratch, nrhs, nblk, out);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_f64_to_f32_scaled(const double2* x, const double* scale, float2* y, int64_t N,
+                              int nrhs, cudaStream_t st) {
+    f64_to_f32_scaled_kernel<<<nblocks(N * nrhs), 256, 0, st>>>(x, scale, y, N, nrhs);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_axpy_f32_into_f64(const float2* d, const double* scale, double2* x, int64_t N,
+                              int nrhs, cudaStream_t st) {
+    axpy_f32_into_f64_kernel<<<nblocks(N * nrhs), 256, 0, st>>>(d, scale, x, N, nrhs);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_sub64(const double2* b, const double2* ax, double2* r, int64_t N, int nrhs,
+                  cudaStream_t st) {
+    sub64_kernel<<<nblocks(N * nrhs), 256, 0, st>>>(b, ax, r, N * nrhs);
+    MBS_CHECK_LAUNCH();
+}
+
+template <typename V>
+void launch_sub(const V* b, const V* ax, V* r, int64_t n, cudaStream_t st) {
+    if (n == 0) return;
+    sub_kernel<V><<<nblocks(n), 256, 0, st>>>(b, ax, r, n);
+    MBS_CHECK_LAUNCH();
+}
+template void launch_sub<float2>(const float2*, const float2*, float2*, int64_t, cudaStream_t);
+template void launch_sub<double2>(const double2*, const double2*, double2*, int64_t, cudaStream_t);
+
+void launch_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t st) {
+    if (n == 0) return;
+    f32_to_f64_kernel<<<nblocks(n), 256, 0, st>>>(a, b, n);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st) {
+    if (n == 0) return;
+    f64_to_f32_kernel<<<nblocks(n), 256, 0, st>>>(a, b, n);
+    MBS_CHECK_LAUNCH();
+}

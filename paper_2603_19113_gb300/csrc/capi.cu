@@ -1,0 +1,1201 @@
+// C ABI of the multibody scattering library: context, S build driver,
+// layout, right-hand side, operator, GMRES / GMRES-IR solve and field
+// evaluation.  See include/mbs.h for the contract of every call.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "sbuild.cuh"
+
+namespace {
+
+using cd = std::complex<double>;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct ShapeHost {
+    int m = 0, n = 0, p = 0, kfix = 0;
+    double eps = 0, proxy_radius = 0, bound_radius = 0;
+    std::vector<double> x, y, z;  // SoA local coordinates
+    bool used = false;
+    int k = 0, rankA = 0, rankB = 0;
+    double eps_ach = 0;
+    std::vector<int> skel;
+    // device (owned by the context allocation list)
+    double *dx = nullptr, *dy = nullptr, *dz = nullptr;
+    double2 *AU = nullptr, *diagA = nullptr, *Zs = nullptr, *C = nullptr, *S64 = nullptr,
+            *W = nullptr;
+    float2* S32 = nullptr;
+    int* permA = nullptr;
+};
+
+}  // namespace
+
+struct mbs_ctx {
+    int dim = 2;
+    double kappa = 1.0;
+    mbs_options opt{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::mutex mu;
+    std::string err;
+
+    // geometry
+    std::vector<ShapeHost> shapes;
+    std::vector<mbs_body> bodies;
+    int T = 0;
+    int64_t N = 0, Mtot = 0;
+    std::vector<int64_t> off, voff;
+    std::vector<int> kb;  // per-body skeleton count
+    std::vector<double> skel_world;  // dim * N SoA
+    bool built = false;
+    int kmax = 0, mmax = 0, nmax = 0;
+
+    // device layout
+    int* d_body = nullptr;
+    int64_t* d_off = nullptr;
+    float* d_loc32 = nullptr;
+    double* d_xw64 = nullptr;
+    float4* d_pair = nullptr;
+    float* d_pair_phi0 = nullptr;
+    double* d_centres = nullptr;
+    int* d_k = nullptr;
+    const double2** d_S64p = nullptr;
+    const float2** d_S32p = nullptr;
+    RhsBody* d_rhsb = nullptr;
+    std::map<std::pair<int64_t, int>, int*> split_cache;  // (targets, nsplit) -> split_body
+
+    // allocations
+    std::vector<void*> geom_allocs;  // freed on rebuild
+    std::unordered_map<std::string, DevBuf> bufs;
+    size_t bytes_held = 0;
+    std::map<void*, size_t> sizes;
+};
+
+namespace {
+
+void* dalloc(mbs_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c->opt.hbm_budget && c->bytes_held + bytes > c->opt.hbm_budget)
+        throw MbsError{MBS_ERR_NOMEM, "HBM budget exceeded (" + std::to_string(c->bytes_held + bytes) +
+                                          " > " + std::to_string(c->opt.hbm_budget) + " bytes)"};
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw MbsError{MBS_ERR_NOMEM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                          "): " + cudaGetErrorString(e)};
+    }
+    c->bytes_held += bytes;
+    c->sizes[p] = bytes;
+    return p;
+}
+
+void dfree(mbs_ctx* c, void* p) {
+    if (!p) return;
+    auto it = c->sizes.find(p);
+    if (it != c->sizes.end()) {
+        c->bytes_held -= it->second;
+        c->sizes.erase(it);
+    }
+    cudaFree(p);
+}
+
+template <typename T>
+T* galloc(mbs_ctx* c, size_t count) {
+    T* p = static_cast<T*>(dalloc(c, count * sizeof(T)));
+    c->geom_allocs.push_back(p);
+    return p;
+}
+
+template <typename T>
+T* scratch(mbs_ctx* c, const std::string& name, size_t count) {
+    DevBuf& b = c->bufs[name];
+    const size_t need = count * sizeof(T);
+    if (b.n < need) {
+        if (b.p) {
+            MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+            dfree(c, b.p);
+            b.p = nullptr;
+            b.n = 0;
+        }
+        b.p = dalloc(c, need);
+        b.n = need;
+    }
+    return static_cast<T*>(b.p);
+}
+
+void free_geometry(mbs_ctx* c) {
+    if (c->st) cudaStreamSynchronize(c->st);
+    for (void* p : c->geom_allocs) dfree(c, p);
+    c->geom_allocs.clear();
+    for (auto& kv : c->split_cache) dfree(c, kv.second);
+    c->split_cache.clear();
+    c->shapes.clear();
+    c->bodies.clear();
+    c->built = false;
+    c->T = 0;
+    c->N = 0;
+    c->d_body = nullptr;
+    c->d_off = nullptr;
+    c->d_loc32 = nullptr;
+    c->d_xw64 = nullptr;
+    c->d_pair = nullptr;
+    c->d_pair_phi0 = nullptr;
+    c->d_centres = nullptr;
+    c->d_k = nullptr;
+    c->d_S64p = nullptr;
+    c->d_S32p = nullptr;
+    c->d_rhsb = nullptr;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller's complex input array (copied if it lives on the host).
+const double2* in_dev(mbs_ctx* c, const double* p, size_t ncomplex, const char* name) {
+    if (is_device_ptr(p)) return reinterpret_cast<const double2*>(p);
+    double2* d = scratch<double2>(c, name, ncomplex);
+    MBS_CUDA_TRY(cudaMemcpyAsync(d, p, ncomplex * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    return d;
+}
+const double* in_dev_real(mbs_ctx* c, const double* p, size_t n, const char* name) {
+    if (is_device_ptr(p)) return p;
+    double* d = scratch<double>(c, name, n);
+    MBS_CUDA_TRY(cudaMemcpyAsync(d, p, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    return d;
+}
+
+struct OutBuf {
+    double* user;
+    double2* dev;
+    size_t n;
+    bool host;
+};
+OutBuf out_dev(mbs_ctx* c, double* p, size_t ncomplex, const char* name) {
+    OutBuf o{p, nullptr, ncomplex, !is_device_ptr(p)};
+    o.dev = o.host ? scratch<double2>(c, name, ncomplex) : reinterpret_cast<double2*>(p);
+    return o;
+}
+void finish_out(mbs_ctx* c, const OutBuf& o) {
+    if (o.host)
+        MBS_CUDA_TRY(cudaMemcpyAsync(o.user, o.dev, o.n * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+    MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+}
+
+void require_built(mbs_ctx* c) {
+    if (!c->built) throw MbsError{MBS_ERR_STATE, "scattering matrices not built"};
+}
+
+// ---------------------------------------------------------------------------
+// launch-shape helpers
+// ---------------------------------------------------------------------------
+int choose_nsplit(mbs_ctx* c, int64_t ntargets) {
+    if (c->opt.tile_override > 0) return std::min(c->opt.tile_override, std::max(1, c->T));
+    const int64_t tiles = (ntargets + 255) / 256;
+    const int64_t want = 16LL * mbs_num_sms();
+    int64_t ns = (want + tiles - 1) / std::max<int64_t>(1, tiles);
+    ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min(c->T, 64)));
+    return (int)ns;
+}
+
+// split_body[s] = first source body of split s, balanced by skeleton counts.
+int* split_for(mbs_ctx* c, int64_t ntargets, int* nsplit_out) {
+    const int ns = choose_nsplit(c, ntargets);
+    *nsplit_out = ns;
+    auto key = std::make_pair((int64_t)ns, 0);
+    auto it = c->split_cache.find(key);
+    if (it != c->split_cache.end()) return it->second;
+    std::vector<int> sb(ns + 1, c->T);
+    sb[0] = 0;
+    int b = 0;
+    for (int s = 1; s < ns; ++s) {
+        const int64_t target = (c->N * s) / ns;
+        while (b < c->T && c->off[b] < target) ++b;
+        sb[s] = std::max(sb[s - 1], std::min(b, c->T));
+    }
+    sb[ns] = c->T;
+    int* d = static_cast<int*>(dalloc(c, sb.size() * sizeof(int)));
+    MBS_CUDA_TRY(cudaMemcpy(d, sb.data(), sb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->split_cache[key] = d;
+    return d;
+}
+
+GLayout glayout(mbs_ctx* c) {
+    GLayout L;
+    L.dim = c->dim;
+    L.T = c->T;
+    L.N = c->N;
+    L.body = c->d_body;
+    L.off = c->d_off;
+    L.loc32 = c->d_loc32;
+    L.xw64 = c->d_xw64;
+    L.pair = c->d_pair;
+    L.pair_phi0 = c->d_pair_phi0;
+    return L;
+}
+
+SBlocks sblocks(mbs_ctx* c) {
+    SBlocks B;
+    B.T = c->T;
+    B.k = c->d_k;
+    B.off = c->d_off;
+    B.S64 = c->d_S64p;
+    B.S32 = c->d_S32p;
+    return B;
+}
+
+// y = G_hat x (FP32)
+void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
+    int ns;
+    int* sb = split_for(c, c->N, &ns);
+    float2* part = scratch<float2>(c, "part32", (size_t)ns * nrhs * c->N);
+    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st);
+}
+void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
+    int ns;
+    int* sb = split_for(c, c->N, &ns);
+    double2* part = scratch<double2>(c, "part64", (size_t)ns * nrhs * c->N);
+    launch_G_f64(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st);
+}
+
+// out = x + S G_hat x
+void op32(mbs_ctx* c, int nrhs, const float2* x, float2* out) {
+    float2* t = scratch<float2>(c, "op_t32", (size_t)nrhs * c->N);
+    G32(c, nrhs, x, t);
+    launch_sapply_f32(sblocks(c), c->N, nrhs, x, t, out, c->kmax, c->st);
+}
+void op64(mbs_ctx* c, int nrhs, const double2* x, double2* out) {
+    double2* t = scratch<double2>(c, "op_t64", (size_t)nrhs * c->N);
+    G64(c, nrhs, x, t);
+    launch_sapply_f64(sblocks(c), c->N, nrhs, x, t, out, c->kmax, c->st);
+}
+
+template <typename V>
+void apply_op(mbs_ctx* c, int nrhs, const V* x, V* out);
+template <>
+void apply_op<float2>(mbs_ctx* c, int nrhs, const float2* x, float2* out) {
+    op32(c, nrhs, x, out);
+}
+template <>
+void apply_op<double2>(mbs_ctx* c, int nrhs, const double2* x, double2* out) {
+    op64(c, nrhs, x, out);
+}
+
+int dot_blocks(int64_t N) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((N + 1023) / 1024, 2LL * mbs_num_sms()));
+}
+
+// Per-RHS 2-norms of a [nrhs][N] vector block (host result).
+template <typename V>
+std::vector<double> norms(mbs_ctx* c, const V* x, int nrhs) {
+    const int nb = dot_blocks(c->N);
+    double2* d = scratch<double2>(c, "nrm_out", nrhs);
+    double2* sc = scratch<double2>(c, "nrm_sc", (size_t)nrhs * nb);
+    std::vector<double2> h(nrhs);
+    // the "basis" is x itself with one vector per RHS: dots(x_r, x_r) for each r
+    std::vector<double> out(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+        launch_dots<V>(x + (int64_t)r * c->N, 1, x + (int64_t)r * c->N, c->N, 1, d + r, sc, nb, c->st);
+    }
+    MBS_CUDA_TRY(cudaMemcpyAsync(h.data(), d, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+    MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+    for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, h[r].x));
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// restarted GMRES on (I + S G) x = b for nrhs independent right-hand sides,
+// advanced in lockstep (one operator application covers every RHS).
+// Arnoldi with classical Gram-Schmidt applied twice (CGS2), complex Givens
+// rotations on the Hessenberg matrices on the host (FP64).
+// ---------------------------------------------------------------------------
+struct GmresStats {
+    int iters = 0;
+    int matvecs = 0;
+    std::vector<double> relres;  // estimate (rotations) per RHS at exit
+    bool converged = false;
+};
+
+template <typename V>
+GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol, int restart,
+                 int maxit, bool verify) {
+    const int64_t N = c->N;
+    const size_t NV = (size_t)nrhs * N;
+    GmresStats S;
+    S.relres.assign(nrhs, 0.0);
+    V* basis = scratch<V>(c, std::string("gm_basis") + (sizeof(V) == 8 ? "32" : "64"),
+                          (size_t)(restart + 1) * NV);
+    V* w = scratch<V>(c, std::string("gm_w") + (sizeof(V) == 8 ? "32" : "64"), NV);
+    V* r = scratch<V>(c, std::string("gm_r") + (sizeof(V) == 8 ? "32" : "64"), NV);
+    const int nb = dot_blocks(N);
+    double2* d_h = scratch<double2>(c, "gm_h", (size_t)(2 * (restart + 1) + 1) * nrhs);
+    double2* d_sc = scratch<double2>(c, "gm_sc", (size_t)(restart + 1) * nrhs * nb);
+    double* d_inv = scratch<double>(c, "gm_inv", nrhs);
+
+    const std::vector<double> bn = norms<V>(c, b, nrhs);
+    // initial residual
+    if (x_zero) {
+        MBS_CUDA_TRY(cudaMemsetAsync(x, 0, NV * sizeof(V), c->st));
+        MBS_CUDA_TRY(cudaMemcpyAsync(r, b, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        apply_op<V>(c, nrhs, x, w);
+        S.matvecs++;
+        launch_sub<V>(b, w, r, (int64_t)NV, c->st);
+    }
+    const int ld = restart + 1;
+    std::vector<cd> H((size_t)nrhs * ld * restart), cs(nrhs * restart), sn(nrhs * restart),
+        g((size_t)nrhs * ld);
+    std::vector<double2> hh((size_t)(2 * (restart + 1) + 1) * nrhs);
+    std::vector<double> inv(nrhs);
+    std::vector<int> msteps(nrhs), frozen(nrhs);
+    while (true) {
+        std::vector<double> beta = norms<V>(c, r, nrhs);
+        bool all = true;
+        for (int q = 0; q < nrhs; ++q) {
+            const double rel = bn[q] > 0 ? beta[q] / bn[q] : 0.0;
+            S.relres[q] = rel;
+            frozen[q] = rel <= tol ? 1 : 0;
+            all = all && frozen[q];
+            inv[q] = frozen[q] ? 0.0 : 1.0 / beta[q];
+            msteps[q] = 0;
+            for (int i = 0; i < ld; ++i) g[(size_t)q * ld + i] = 0.0;
+            g[(size_t)q * ld] = frozen[q] ? 0.0 : beta[q];
+        }
+        if (all) {
+            S.converged = true;
+            break;
+        }
+        if (S.iters >= maxit) break;
+        MBS_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        launch_scale<V>(r, d_inv, basis, N, nrhs, c->st);
+        int jdone = 0;
+        for (int j = 0; j < restart && S.iters < maxit; ++j) {
+            V* vj = basis + (size_t)j * NV;
+            apply_op<V>(c, nrhs, vj, w);
+            S.matvecs++;
+            double2* h1 = d_h;
+            double2* h2 = d_h + (size_t)(restart + 1) * nrhs;
+            double2* hn = d_h + (size_t)2 * (restart + 1) * nrhs;
+            launch_dots<V>(basis, j + 1, w, N, nrhs, h1, d_sc, nb, c->st);
+            launch_update<V>(basis, j + 1, h1, w, N, nrhs, -1.0, c->st);
+            launch_dots<V>(basis, j + 1, w, N, nrhs, h2, d_sc, nb, c->st);
+            launch_update<V>(basis, j + 1, h2, w, N, nrhs, -1.0, c->st);
+            for (int q = 0; q < nrhs; ++q)
+                launch_dots<V>(w + (size_t)q * N, 1, w + (size_t)q * N, N, 1, hn + q, d_sc, nb, c->st);
+            MBS_CUDA_TRY(cudaMemcpyAsync(hh.data(), d_h, hh.size() * sizeof(double2),
+                                         cudaMemcpyDeviceToHost, c->st));
+            MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+            S.iters++;
+            jdone = j + 1;
+            bool allf = true;
+            for (int q = 0; q < nrhs; ++q) {
+                if (frozen[q]) {
+                    inv[q] = 0.0;
+                    continue;
+                }
+                cd* Hq = &H[(size_t)q * ld * restart];
+                cd* col = Hq + (size_t)j * ld;
+                for (int i = 0; i <= j; ++i) {
+                    const double2 a = hh[(size_t)i * nrhs + q];
+                    const double2 bb = hh[(size_t)(restart + 1) * nrhs + (size_t)i * nrhs + q];
+                    col[i] = cd(a.x + bb.x, a.y + bb.y);
+                }
+                const double hnext = std::sqrt(std::max(0.0, hh[(size_t)2 * (restart + 1) * nrhs + q].x));
+                col[j + 1] = hnext;
+                cd* csq = &cs[(size_t)q * restart];
+                cd* snq = &sn[(size_t)q * restart];
+                cd* gq = &g[(size_t)q * ld];
+                for (int i = 0; i < j; ++i) {
+                    const cd t = std::conj(csq[i]) * col[i] + std::conj(snq[i]) * col[i + 1];
+                    col[i + 1] = -snq[i] * col[i] + csq[i] * col[i + 1];
+                    col[i] = t;
+                }
+                const cd a = col[j], bb = col[j + 1];
+                const double den = std::sqrt(std::norm(a) + std::norm(bb));
+                csq[j] = den > 0 ? a / den : cd(1.0);
+                snq[j] = den > 0 ? bb / den : cd(0.0);
+                col[j] = den;
+                col[j + 1] = 0.0;
+                gq[j + 1] = -snq[j] * gq[j];
+                gq[j] = std::conj(csq[j]) * gq[j];
+                msteps[q] = j + 1;
+                const double rel = bn[q] > 0 ? std::abs(gq[j + 1]) / bn[q] : 0.0;
+                S.relres[q] = rel;
+                const bool breakdown = hnext <= 1e-300 || hnext <= 1e-15 * den;
+                if (rel <= tol || breakdown) {
+                    frozen[q] = 1;
+                    inv[q] = 0.0;
+                } else {
+                    inv[q] = 1.0 / hnext;
+                    allf = false;
+                }
+            }
+            if (allf) break;
+            if (j + 1 < restart) {
+                MBS_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), nrhs * sizeof(double),
+                                             cudaMemcpyHostToDevice, c->st));
+                launch_scale<V>(w, d_inv, basis + (size_t)(j + 1) * NV, N, nrhs, c->st);
+            }
+        }
+        // x += V y with y from the triangular systems
+        std::vector<double2> y((size_t)jdone * nrhs, make_double2(0.0, 0.0));
+        for (int q = 0; q < nrhs; ++q) {
+            const int mq = msteps[q];
+            const cd* Hq = &H[(size_t)q * ld * restart];
+            const cd* gq = &g[(size_t)q * ld];
+            std::vector<cd> yq(mq);
+            for (int i = mq - 1; i >= 0; --i) {
+                cd s = gq[i];
+                for (int l = i + 1; l < mq; ++l) s -= Hq[(size_t)l * ld + i] * yq[l];
+                yq[i] = s / Hq[(size_t)i * ld + i];
+            }
+            for (int i = 0; i < mq; ++i) y[(size_t)i * nrhs + q] = make_double2(yq[i].real(), yq[i].imag());
+        }
+        if (jdone > 0) {
+            MBS_CUDA_TRY(cudaMemcpyAsync(d_h, y.data(), y.size() * sizeof(double2),
+                                         cudaMemcpyHostToDevice, c->st));
+            launch_update<V>(basis, jdone, d_h, x, N, nrhs, 1.0, c->st);
+        }
+        bool est_conv = true;
+        for (int q = 0; q < nrhs; ++q) est_conv = est_conv && S.relres[q] <= tol;
+        if (est_conv && !verify) {
+            S.converged = true;
+            break;
+        }
+        if (S.iters >= maxit && !verify) break;
+        // true residual, then restart (or final check)
+        apply_op<V>(c, nrhs, x, w);
+        S.matvecs++;
+        launch_sub<V>(b, w, r, (int64_t)NV, c->st);
+        if (S.iters >= maxit) {
+            std::vector<double> beta = norms<V>(c, r, nrhs);
+            bool ok = true;
+            for (int q = 0; q < nrhs; ++q) {
+                S.relres[q] = bn[q] > 0 ? beta[q] / bn[q] : 0.0;
+                ok = ok && S.relres[q] <= tol;
+            }
+            S.converged = ok;
+            break;
+        }
+    }
+    return S;
+}
+
+void validate_options(const mbs_options& o) {
+    if (o.precision != MBS_PREC_FP64 && o.precision != MBS_PREC_MIXED && o.precision != MBS_PREC_FP32)
+        throw MbsError{MBS_ERR_ARG, "precision must be MBS_PREC_FP64, MBS_PREC_MIXED or MBS_PREC_FP32"};
+    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.restart < 1 || o.max_iter < 1 || o.max_sweeps < 1 ||
+        !(o.ls_rcond > 0 && o.ls_rcond < 1))
+        throw MbsError{MBS_ERR_ARG, "invalid tolerance / restart / iteration options"};
+}
+
+template <typename F>
+mbs_status guarded(mbs_ctx* c, F&& f) {
+    if (!c) return MBS_ERR_ARG;
+    std::lock_guard<std::mutex> g(c->mu);
+    try {
+        const mbs_status s = f();
+        if (s == MBS_OK) c->err.clear();
+        return s;
+    } catch (const MbsError& e) {
+        c->err = e.msg;
+        return e.st;
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return MBS_ERR_CUDA;
+    }
+}
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void world_point(const mbs_body& B, int dim, const double* loc, double* out) {
+    for (int a = 0; a < dim; ++a) {
+        double s = B.c[a];
+        for (int b2 = 0; b2 < dim; ++b2) s += B.R[3 * a + b2] * loc[b2];
+        out[a] = s;
+    }
+}
+
+// Every collocation point of every body must lie strictly outside the proxy
+// radius of every other body (Sec. 4.1: S_tau handles sources outside Psi_tau).
+void check_geometry(mbs_ctx* c) {
+    const int T = c->T, d = c->dim;
+    double reach = 0;
+    for (int t = 0; t < T; ++t) {
+        const ShapeHost& s = c->shapes[c->bodies[t].shape];
+        reach = std::max(reach, s.proxy_radius + s.bound_radius);
+    }
+    const double h = std::max(reach, 1e-12);
+    std::unordered_map<int64_t, std::vector<int>> grid;
+    auto key = [&](int64_t ix, int64_t iy, int64_t iz) {
+        return ((ix & 0x1FFFFF) << 42) | ((iy & 0x1FFFFF) << 21) | (iz & 0x1FFFFF);
+    };
+    for (int t = 0; t < T; ++t) {
+        const double* cc = c->bodies[t].c;
+        grid[key((int64_t)std::floor(cc[0] / h), (int64_t)std::floor(cc[1] / h),
+                 d == 3 ? (int64_t)std::floor(cc[2] / h) : 0)]
+            .push_back(t);
+    }
+    std::vector<double> loc(3), wp(3);
+    for (int t = 0; t < T; ++t) {
+        const mbs_body& Bt = c->bodies[t];
+        const ShapeHost& st = c->shapes[Bt.shape];
+        const int64_t ix = (int64_t)std::floor(Bt.c[0] / h), iy = (int64_t)std::floor(Bt.c[1] / h),
+                      iz = d == 3 ? (int64_t)std::floor(Bt.c[2] / h) : 0;
+        for (int64_t a = -1; a <= 1; ++a)
+            for (int64_t b2 = -1; b2 <= 1; ++b2)
+                for (int64_t e = (d == 3 ? -1 : 0); e <= (d == 3 ? 1 : 0); ++e) {
+                    auto it = grid.find(key(ix + a, iy + b2, iz + e));
+                    if (it == grid.end()) continue;
+                    for (int s : it->second) {
+                        if (s == t) continue;
+                        const mbs_body& Bs = c->bodies[s];
+                        const ShapeHost& ss = c->shapes[Bs.shape];
+                        double cd2 = 0;
+                        for (int q = 0; q < d; ++q) cd2 += (Bt.c[q] - Bs.c[q]) * (Bt.c[q] - Bs.c[q]);
+                        const double lim = st.proxy_radius + ss.bound_radius;
+                        if (cd2 > lim * lim) continue;
+                        for (int i = 0; i < ss.m; ++i) {
+                            for (int q = 0; q < d; ++q) loc[q] = ss.x[(size_t)q * ss.m + i];
+                            world_point(Bs, d, loc.data(), wp.data());
+                            double r2 = 0;
+                            for (int q = 0; q < d; ++q) r2 += (wp[q] - Bt.c[q]) * (wp[q] - Bt.c[q]);
+                            if (r2 <= st.proxy_radius * st.proxy_radius)
+                                throw MbsError{MBS_ERR_GEOMETRY,
+                                               "body " + std::to_string(s) +
+                                                   " reaches inside the proxy surface of body " +
+                                                   std::to_string(t)};
+                        }
+                    }
+                }
+    }
+}
+
+// Skeleton layout, body-pair table, S pointer tables, right-hand-side descriptors.
+void setup_layout(mbs_ctx* c) {
+    const int T = c->T, d = c->dim;
+    c->off.assign(T + 1, 0);
+    c->voff.assign(T + 1, 0);
+    c->kb.assign(T, 0);
+    c->kmax = c->mmax = c->nmax = 0;
+    for (int t = 0; t < T; ++t) {
+        const ShapeHost& s = c->shapes[c->bodies[t].shape];
+        c->kb[t] = s.k;
+        c->off[t + 1] = c->off[t] + s.k;
+        c->voff[t + 1] = c->voff[t] + s.m;
+        c->kmax = std::max(c->kmax, s.k);
+        c->mmax = std::max(c->mmax, s.m);
+        c->nmax = std::max(c->nmax, s.n);
+    }
+    c->N = c->off[T];
+    c->Mtot = c->voff[T];
+    const int64_t N = c->N;
+    std::vector<int> body(N);
+    std::vector<float> loc32((size_t)d * N);
+    c->skel_world.assign((size_t)d * N, 0.0);
+    std::vector<double> cen((size_t)3 * T, 0.0);
+    for (int t = 0; t < T; ++t) {
+        const mbs_body& B = c->bodies[t];
+        const ShapeHost& s = c->shapes[B.shape];
+        for (int a = 0; a < 3; ++a) cen[3 * t + a] = (a < d) ? B.c[a] : 0.0;
+        for (int i = 0; i < s.k; ++i) {
+            const int64_t g = c->off[t] + i;
+            body[g] = t;
+            const int col = s.skel[i];
+            for (int a = 0; a < d; ++a) {
+                double dl = 0.0;
+                for (int b2 = 0; b2 < d; ++b2) dl += B.R[3 * a + b2] * s.x[(size_t)b2 * s.m + col];
+                loc32[(size_t)a * N + g] = (float)dl;
+                c->skel_world[(size_t)a * N + g] = B.c[a] + dl;
+            }
+        }
+    }
+    c->d_body = galloc<int>(c, N);
+    c->d_off = galloc<int64_t>(c, T + 1);
+    c->d_loc32 = galloc<float>(c, (size_t)d * N);
+    c->d_xw64 = galloc<double>(c, (size_t)d * N);
+    c->d_centres = galloc<double>(c, (size_t)3 * T);
+    c->d_pair = galloc<float4>(c, (size_t)T * T);
+    c->d_pair_phi0 = d == 3 ? galloc<float>(c, (size_t)T * T) : nullptr;
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_body, body.data(), N * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_off, c->off.data(), (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_loc32, loc32.data(), loc32.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_xw64, c->skel_world.data(), c->skel_world.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_centres, cen.data(), cen.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_pair_table(d, T, c->d_centres, c->kappa, c->d_pair, c->d_pair_phi0, c->st);
+    // S tables and RHS descriptors
+    std::vector<const double2*> s64(T);
+    std::vector<const float2*> s32(T);
+    std::vector<RhsBody> rb(T);
+    for (int t = 0; t < T; ++t) {
+        const ShapeHost& s = c->shapes[c->bodies[t].shape];
+        s64[t] = s.S64;
+        s32[t] = s.S32;
+        RhsBody& R = rb[t];
+        R.m = s.m;
+        R.n = s.n;
+        R.k = s.k;
+        R.rankA = s.rankA;
+        R.voff = c->voff[t];
+        R.boff = c->off[t];
+        R.A = s.AU;
+        R.diagA = s.diagA;
+        R.permA = s.permA;
+        R.C = s.C;
+        R.Zs = s.Zs;
+        R.W = s.W;
+    }
+    c->d_k = galloc<int>(c, T);
+    c->d_S64p = (const double2**)galloc<void*>(c, T);
+    c->d_S32p = (const float2**)galloc<void*>(c, T);
+    c->d_rhsb = galloc<RhsBody>(c, T);
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_k, c->kb.data(), T * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync((void*)c->d_S64p, s64.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync((void*)c->d_S32p, s32.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c->st));
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_rhsb, rb.data(), T * sizeof(RhsBody), cudaMemcpyHostToDevice, c->st));
+    for (auto& kv : c->split_cache) dfree(c, kv.second);
+    c->split_cache.clear();
+    MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+}
+
+void refresh_layout(mbs_ctx* c) {
+    // drop the previous layout allocations (keep shape data) and rebuild
+    MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+    std::vector<void*> keep;
+    const void* lay[] = {c->d_body, c->d_off, c->d_loc32, c->d_xw64, c->d_centres, c->d_pair,
+                         c->d_pair_phi0, c->d_k, c->d_S64p, c->d_S32p, c->d_rhsb};
+    for (void* p : c->geom_allocs) {
+        bool is_lay = false;
+        for (const void* q : lay)
+            if (q == p) is_lay = true;
+        if (is_lay)
+            dfree(c, p);
+        else
+            keep.push_back(p);
+    }
+    c->geom_allocs = keep;
+    setup_layout(c);
+}
+
+void build(mbs_ctx* c, int nshapes, const mbs_shape* shapes, int nbodies, const mbs_body* bodies) {
+    const int d = c->dim;
+    if (nshapes < 1 || !shapes || nbodies < 1 || !bodies)
+        throw MbsError{MBS_ERR_ARG, "need at least one shape and one body"};
+    std::vector<ShapeHost> hs(nshapes);
+    for (int s = 0; s < nshapes; ++s) {
+        const mbs_shape& in = shapes[s];
+        ShapeHost& h = hs[s];
+        if (in.m < 2 || in.n < 1 || in.n >= in.m || in.p < 1 || !in.x || !in.y || !in.z)
+            throw MbsError{MBS_ERR_ARG, "shape " + std::to_string(s) + ": need 0 < n < m, p > 0 and point arrays"};
+        if (in.k < 0 || in.k > std::min(in.m, in.p) || (in.k == 0 && !(in.eps > 0 && in.eps < 1)))
+            throw MbsError{MBS_ERR_ARG, "shape " + std::to_string(s) + ": need 0 < k <= min(m, p) or 0 < eps < 1"};
+        if (!(in.proxy_radius > 0))
+            throw MbsError{MBS_ERR_ARG, "shape " + std::to_string(s) + ": proxy_radius must be > 0"};
+        h.m = in.m;
+        h.n = in.n;
+        h.p = in.p;
+        h.kfix = in.k;
+        h.eps = in.eps;
+        h.proxy_radius = in.proxy_radius;
+        h.x.assign(in.x, in.x + (size_t)d * in.m);
+        h.y.assign(in.y, in.y + (size_t)d * in.n);
+        h.z.assign(in.z, in.z + (size_t)d * in.p);
+        if (!finite_all(h.x.data(), h.x.size()) || !finite_all(h.y.data(), h.y.size()) ||
+            !finite_all(h.z.data(), h.z.size()))
+            throw MbsError{MBS_ERR_ARG, "shape " + std::to_string(s) + ": non-finite coordinates"};
+        double br = 0;
+        for (int i = 0; i < in.m; ++i) {
+            double r2 = 0;
+            for (int a = 0; a < d; ++a) r2 += h.x[(size_t)a * in.m + i] * h.x[(size_t)a * in.m + i];
+            br = std::max(br, std::sqrt(r2));
+        }
+        h.bound_radius = br;
+    }
+    std::vector<mbs_body> hb(bodies, bodies + nbodies);
+    for (int t = 0; t < nbodies; ++t) {
+        if (hb[t].shape < 0 || hb[t].shape >= nshapes)
+            throw MbsError{MBS_ERR_ARG, "body " + std::to_string(t) + ": bad shape index"};
+        if (!finite_all(hb[t].c, 3) || !finite_all(hb[t].R, 9))
+            throw MbsError{MBS_ERR_ARG, "body " + std::to_string(t) + ": non-finite placement"};
+        hs[hb[t].shape].used = true;
+    }
+    free_geometry(c);
+    c->shapes = std::move(hs);
+    c->bodies = std::move(hb);
+    c->T = nbodies;
+    check_geometry(c);
+
+    // jobs for the used shapes, in batches bounded by a workspace budget
+    std::vector<int> used;
+    for (int s = 0; s < nshapes; ++s)
+        if (c->shapes[s].used) used.push_back(s);
+    std::sort(used.begin(), used.end(), [&](int a, int b2) {
+        return (int64_t)c->shapes[a].m * c->shapes[a].p > (int64_t)c->shapes[b2].m * c->shapes[b2].p;
+    });
+    const size_t ws_budget = (size_t)8 << 30;
+    size_t pos = 0;
+    while (pos < used.size()) {
+        std::vector<int> batch;
+        size_t ws = 0;
+        while (pos < used.size()) {
+            const ShapeHost& s = c->shapes[used[pos]];
+            const int kcap = s.kfix > 0 ? s.kfix : std::min(s.m, s.p);
+            const size_t need = sizeof(double2) * ((size_t)s.p * (s.m + s.n) + (size_t)kcap * std::max(s.m, s.n) +
+                                                   (size_t)std::min(s.p, s.m) * s.n + s.p + s.m);
+            if (!batch.empty() && ws + need > ws_budget) break;
+            batch.push_back(used[pos++]);
+            ws += need;
+        }
+        const int nj = (int)batch.size();
+        std::vector<SBuildJob> jobs(nj);
+        std::vector<void*> tmp;
+        auto talloc = [&](size_t bytes) {
+            void* p = dalloc(c, bytes);
+            tmp.push_back(p);
+            return p;
+        };
+        int pmax = 1, mmax = 1;
+        for (int j = 0; j < nj; ++j) {
+            ShapeHost& s = c->shapes[batch[j]];
+            SBuildJob& J = jobs[j];
+            std::memset(&J, 0, sizeof(J));
+            const int kcap = s.kfix > 0 ? s.kfix : std::min(s.m, s.p);
+            J.m = s.m;
+            J.n = s.n;
+            J.p = s.p;
+            J.kfix = s.kfix;
+            J.eps = s.eps;
+            s.dx = galloc<double>(c, s.x.size());
+            s.dy = galloc<double>(c, s.y.size());
+            s.dz = galloc<double>(c, s.z.size());
+            MBS_CUDA_TRY(cudaMemcpyAsync(s.dx, s.x.data(), s.x.size() * 8, cudaMemcpyHostToDevice, c->st));
+            MBS_CUDA_TRY(cudaMemcpyAsync(s.dy, s.y.data(), s.y.size() * 8, cudaMemcpyHostToDevice, c->st));
+            MBS_CUDA_TRY(cudaMemcpyAsync(s.dz, s.z.data(), s.z.size() * 8, cudaMemcpyHostToDevice, c->st));
+            J.x = s.dx;
+            J.y = s.dy;
+            J.z = s.dz;
+            J.BD = (double2*)talloc(sizeof(double2) * (size_t)s.p * (s.m + s.n));
+            s.AU = galloc<double2>(c, (size_t)s.m * (s.n + kcap));
+            J.AU = s.AU;
+            J.W1 = (double2*)talloc(sizeof(double2) * (size_t)kcap * std::max(s.m, s.n));
+            J.W2 = (double2*)talloc(sizeof(double2) * (size_t)std::min(s.p, s.m) * s.n);
+            J.nrm2 = (double*)talloc(sizeof(double) * std::max(s.m, s.n));
+            J.permB = (int*)talloc(sizeof(int) * s.m);
+            J.diagB = (double2*)talloc(sizeof(double2) * std::min(s.p, s.m));
+            s.permA = galloc<int>(c, s.n);
+            s.diagA = galloc<double2>(c, s.n);
+            J.permA = s.permA;
+            J.diagA = s.diagA;
+            J.skel = (int*)talloc(sizeof(int) * kcap);
+            s.Zs = galloc<double2>(c, (size_t)kcap * s.m);
+            s.C = galloc<double2>(c, (size_t)s.m * s.n);
+            s.S64 = galloc<double2>(c, (size_t)kcap * kcap);
+            J.Zs = s.Zs;
+            J.C = s.C;
+            J.S = s.S64;
+            pmax = std::max(pmax, s.p);
+            mmax = std::max(mmax, s.m);
+        }
+        SBuildJob* d_jobs = (SBuildJob*)talloc(sizeof(SBuildJob) * nj);
+        MBS_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(SBuildJob) * nj, cudaMemcpyHostToDevice, c->st));
+        launch_sbuild_phase1(d, d_jobs, nj, pmax, c->kappa, c->opt.ls_rcond, c->st);
+        launch_sbuild_phase2(d_jobs, nj, mmax, c->opt.ls_rcond, c->st);
+        MBS_CUDA_TRY(cudaMemcpyAsync(jobs.data(), d_jobs, sizeof(SBuildJob) * nj, cudaMemcpyDeviceToHost, c->st));
+        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+        for (int j = 0; j < nj; ++j) {
+            ShapeHost& s = c->shapes[batch[j]];
+            const SBuildJob& J = jobs[j];
+            s.k = J.k;
+            s.rankA = J.rankA;
+            s.rankB = J.rankB;
+            s.eps_ach = J.eps_ach;
+            if (s.k < 1) throw MbsError{MBS_ERR_ARG, "shape " + std::to_string(batch[j]) + ": zero skeleton"};
+            s.skel.resize(s.k);
+            MBS_CUDA_TRY(cudaMemcpy(s.skel.data(), J.skel, s.k * sizeof(int), cudaMemcpyDeviceToHost));
+            // Z* and S were written with leading dimension k (<= kcap): already compact.
+            s.S32 = galloc<float2>(c, (size_t)s.k * s.k);
+            launch_f64_to_f32(s.S64, s.S32, (int64_t)s.k * s.k, c->st);
+        }
+        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+        for (void* p : tmp) dfree(c, p);
+    }
+    setup_layout(c);
+    c->built = true;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void mbs_default_options(mbs_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = MBS_PREC_FP64;
+    o->tol = 1e-11;
+    o->inner_tol = 1e-6;
+    o->restart = 60;
+    o->max_iter = 20000;
+    o->max_sweeps = 8;
+    o->ls_rcond = 1e-14;
+    o->stream = nullptr;
+    o->hbm_budget = 0;
+    o->tile_override = 0;
+}
+
+mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {
+    if (!out) return MBS_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || !(kappa > 0) || !std::isfinite(kappa)) return MBS_ERR_ARG;
+    mbs_options o;
+    if (opt)
+        o = *opt;
+    else
+        mbs_default_options(&o);
+    try {
+        validate_options(o);
+    } catch (const MbsError& e) {
+        return e.st;
+    }
+    mbs_ctx* c = new mbs_ctx();
+    c->dim = dim;
+    c->kappa = kappa;
+    c->opt = o;
+    if (o.stream) {
+        c->st = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return MBS_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return MBS_OK;
+}
+
+void mbs_destroy(mbs_ctx* c) {
+    if (!c) return;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        free_geometry(c);
+        for (auto& kv : c->bufs) dfree(c, kv.second.p);
+        c->bufs.clear();
+        if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    }
+    delete c;
+}
+
+mbs_status mbs_set_options(mbs_ctx* c, const mbs_options* opt) {
+    return guarded(c, [&]() {
+        if (!opt) throw MbsError{MBS_ERR_ARG, "null options"};
+        validate_options(*opt);
+        if (opt->stream && opt->stream != (void*)c->st) {
+            if (c->own_stream) {
+                cudaStreamSynchronize(c->st);
+                cudaStreamDestroy(c->st);
+                c->own_stream = false;
+            }
+            c->st = (cudaStream_t)opt->stream;
+        }
+        void* keep = c->opt.stream;
+        c->opt = *opt;
+        if (!opt->stream) c->opt.stream = keep;
+        return MBS_OK;
+    });
+}
+
+const char* mbs_last_error(const mbs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+mbs_status mbs_build_scattering_matrices(mbs_ctx* c, int nshapes, const mbs_shape* shapes,
+                                          int nbodies, const mbs_body* bodies) {
+    return guarded(c, [&]() {
+        build(c, nshapes, shapes, nbodies, bodies);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_get_layout(mbs_ctx* c, int64_t* N, int64_t* body_offsets, double* skel_xyz) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (N) *N = c->N;
+        if (body_offsets) std::memcpy(body_offsets, c->off.data(), (c->T + 1) * sizeof(int64_t));
+        if (skel_xyz) std::memcpy(skel_xyz, c->skel_world.data(), c->skel_world.size() * sizeof(double));
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_get_shape(mbs_ctx* c, int shape, int* k, int* skel, double* S, double* eps_achieved) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (shape < 0 || shape >= (int)c->shapes.size() || !c->shapes[shape].used)
+            throw MbsError{MBS_ERR_ARG, "shape not built"};
+        const ShapeHost& s = c->shapes[shape];
+        if (k) *k = s.k;
+        if (skel) std::memcpy(skel, s.skel.data(), s.k * sizeof(int));
+        if (eps_achieved) *eps_achieved = s.eps_ach;
+        if (S) MBS_CUDA_TRY(cudaMemcpy(S, s.S64, (size_t)s.k * s.k * sizeof(double2), cudaMemcpyDeviceToHost));
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_rhs(mbs_ctx* c, int nrhs, const double* v, double* b) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (nrhs < 1 || !v || !b) throw MbsError{MBS_ERR_ARG, "bad nrhs or null pointer"};
+        const double2* dv = in_dev(c, v, (size_t)c->Mtot * nrhs, "io_v");
+        OutBuf ob = out_dev(c, b, (size_t)c->N * nrhs, "io_b");
+        launch_rhs(c->d_rhsb, c->T, nrhs, c->mmax, c->nmax, dv, c->Mtot, ob.dev, c->N, c->st);
+        finish_out(c, ob);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_apply_G(mbs_ctx* c, int precision, int nrhs, const double* q, double* y) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (nrhs < 1 || !q || !y) throw MbsError{MBS_ERR_ARG, "bad nrhs or null pointer"};
+        const size_t n = (size_t)c->N * nrhs;
+        const double2* dq = in_dev(c, q, n, "io_q");
+        OutBuf oy = out_dev(c, y, n, "io_y");
+        if (precision == MBS_PREC_FP32) {
+            float2* q32 = scratch<float2>(c, "io_q32", n);
+            float2* y32 = scratch<float2>(c, "io_y32", n);
+            launch_f64_to_f32(dq, q32, (int64_t)n, c->st);
+            G32(c, nrhs, q32, y32);
+            launch_f32_to_f64(y32, oy.dev, (int64_t)n, c->st);
+        } else if (precision == MBS_PREC_FP64) {
+            G64(c, nrhs, dq, oy.dev);
+        } else {
+            throw MbsError{MBS_ERR_ARG, "precision must be FP64 or FP32"};
+        }
+        finish_out(c, oy);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_apply_operator(mbs_ctx* c, int nrhs, const double* qhat, double* y) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (nrhs < 1 || !qhat || !y) throw MbsError{MBS_ERR_ARG, "bad nrhs or null pointer"};
+        const size_t n = (size_t)c->N * nrhs;
+        const double2* dq = in_dev(c, qhat, n, "io_q");
+        OutBuf oy = out_dev(c, y, n, "io_y");
+        if (c->opt.precision == MBS_PREC_FP64) {
+            op64(c, nrhs, dq, oy.dev);
+        } else {
+            float2* q32 = scratch<float2>(c, "io_q32", n);
+            float2* y32 = scratch<float2>(c, "io_y32", n);
+            launch_f64_to_f32(dq, q32, (int64_t)n, c->st);
+            op32(c, nrhs, q32, y32);
+            launch_f32_to_f64(y32, oy.dev, (int64_t)n, c->st);
+        }
+        finish_out(c, oy);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_solve_info* info) {
+    return guarded(c, [&]() -> mbs_status {
+        require_built(c);
+        if (nrhs < 1 || !b || !qhat) throw MbsError{MBS_ERR_ARG, "bad nrhs or null pointer"};
+        const auto t0 = std::chrono::steady_clock::now();
+        const size_t n = (size_t)c->N * nrhs;
+        const double2* db = in_dev(c, b, n, "io_b_in");
+        OutBuf ox = out_dev(c, qhat, n, "io_x");
+        if (ox.host)
+            MBS_CUDA_TRY(cudaMemcpyAsync(ox.dev, qhat, n * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+        // is the initial guess zero?
+        std::vector<double> xn = norms<double2>(c, ox.dev, nrhs);
+        bool xzero = true;
+        for (double v : xn) xzero = xzero && v == 0.0;
+        mbs_solve_info inf;
+        std::memset(&inf, 0, sizeof(inf));
+        bool conv = false;
+        double relmax = 0.0;
+        const mbs_options& o = c->opt;
+        if (o.precision == MBS_PREC_FP64 || o.precision == MBS_PREC_FP32) {
+            GmresStats S = gmres<double2>(c, nrhs, db, ox.dev, xzero, o.tol, o.restart, o.max_iter, true);
+            inf.inner_iterations = S.iters;
+            inf.matvecs_fp64 = S.matvecs;
+            inf.sweeps = 1;
+            conv = S.converged;
+            for (double v : S.relres) relmax = std::max(relmax, v);
+        } else {
+            // FP32 GMRES inside FP64 iterative refinement
+            double2* r64 = scratch<double2>(c, "ir_r64", n);
+            double2* t64 = scratch<double2>(c, "ir_t64", n);
+            float2* r32 = scratch<float2>(c, "ir_r32", n);
+            float2* d32 = scratch<float2>(c, "ir_d32", n);
+            double* d_sc = scratch<double>(c, "ir_scale", nrhs);
+            const std::vector<double> bn = norms<double2>(c, db, nrhs);
+            if (xzero) {
+                MBS_CUDA_TRY(cudaMemcpyAsync(r64, db, n * sizeof(double2), cudaMemcpyDeviceToDevice, c->st));
+            } else {
+                op64(c, nrhs, ox.dev, t64);
+                inf.matvecs_fp64++;
+                launch_sub<double2>(db, t64, r64, (int64_t)n, c->st);
+            }
+            std::vector<double> sc(nrhs);
+            while (true) {
+                const std::vector<double> rn = norms<double2>(c, r64, nrhs);
+                relmax = 0.0;
+                bool all = true;
+                for (int q = 0; q < nrhs; ++q) {
+                    const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
+                    relmax = std::max(relmax, rel);
+                    all = all && rel <= o.tol;
+                }
+                if (all) {
+                    conv = true;
+                    break;
+                }
+                if (inf.sweeps >= o.max_sweeps || inf.inner_iterations >= o.max_iter) break;
+                for (int q = 0; q < nrhs; ++q) {
+                    const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
+                    sc[q] = (rel > o.tol && rn[q] > 0) ? 1.0 / rn[q] : 0.0;
+                }
+                MBS_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+                launch_f64_to_f32_scaled(r64, d_sc, r32, c->N, nrhs, c->st);
+                GmresStats S = gmres<float2>(c, nrhs, r32, d32, true, o.inner_tol, o.restart,
+                                             o.max_iter - inf.inner_iterations, false);
+                inf.inner_iterations += S.iters;
+                inf.matvecs_fp32 += S.matvecs;
+                for (int q = 0; q < nrhs; ++q) sc[q] = sc[q] > 0 ? rn[q] : 0.0;
+                MBS_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+                launch_axpy_f32_into_f64(d32, d_sc, ox.dev, c->N, nrhs, c->st);
+                op64(c, nrhs, ox.dev, t64);
+                inf.matvecs_fp64++;
+                launch_sub<double2>(db, t64, r64, (int64_t)n, c->st);
+                inf.sweeps++;
+            }
+        }
+        finish_out(c, ox);
+        inf.converged = conv ? 1 : 0;
+        inf.rel_residual = relmax;
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (info) *info = inf;
+        if (!conv) {
+            c->err = "solve did not reach tol (relative residual " + std::to_string(relmax) + ")";
+            return MBS_ERR_NOCONV;
+        }
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_evaluate_field(mbs_ctx* c, int nrhs, int64_t M, const double* pts,
+                              const double* qhat, double* u) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (nrhs < 1 || M < 0 || (M > 0 && (!pts || !qhat || !u)))
+            throw MbsError{MBS_ERR_ARG, "bad sizes or null pointer"};
+        if (M == 0) return MBS_OK;
+        const int d = c->dim;
+        // targets must lie on or outside every proxy surface
+        std::vector<double> hp((size_t)d * M);
+        if (is_device_ptr(pts))
+            MBS_CUDA_TRY(cudaMemcpy(hp.data(), pts, hp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        else
+            std::memcpy(hp.data(), pts, hp.size() * sizeof(double));
+        if (!finite_all(hp.data(), hp.size())) throw MbsError{MBS_ERR_ARG, "non-finite target"};
+        double reach = 0;
+        for (int t = 0; t < c->T; ++t) reach = std::max(reach, c->shapes[c->bodies[t].shape].proxy_radius);
+        const double h = std::max(reach, 1e-12);
+        std::unordered_map<int64_t, std::vector<int>> grid;
+        auto key = [&](int64_t ix, int64_t iy, int64_t iz) {
+            return ((ix & 0x1FFFFF) << 42) | ((iy & 0x1FFFFF) << 21) | (iz & 0x1FFFFF);
+        };
+        for (int t = 0; t < c->T; ++t) {
+            const double* cc = c->bodies[t].c;
+            grid[key((int64_t)std::floor(cc[0] / h), (int64_t)std::floor(cc[1] / h),
+                     d == 3 ? (int64_t)std::floor(cc[2] / h) : 0)]
+                .push_back(t);
+        }
+        for (int64_t i = 0; i < M; ++i) {
+            double p3[3] = {hp[i], hp[(size_t)M + i], d == 3 ? hp[(size_t)2 * M + i] : 0.0};
+            const int64_t ix = (int64_t)std::floor(p3[0] / h), iy = (int64_t)std::floor(p3[1] / h),
+                          iz = d == 3 ? (int64_t)std::floor(p3[2] / h) : 0;
+            for (int64_t a = -1; a <= 1; ++a)
+                for (int64_t b2 = -1; b2 <= 1; ++b2)
+                    for (int64_t e = (d == 3 ? -1 : 0); e <= (d == 3 ? 1 : 0); ++e) {
+                        auto it = grid.find(key(ix + a, iy + b2, iz + e));
+                        if (it == grid.end()) continue;
+                        for (int t : it->second) {
+                            const double pr = c->shapes[c->bodies[t].shape].proxy_radius;
+                            double r2 = 0;
+                            for (int q = 0; q < d; ++q) r2 += (p3[q] - c->bodies[t].c[q]) * (p3[q] - c->bodies[t].c[q]);
+                            if (r2 < pr * pr * (1.0 - 1e-12))
+                                throw MbsError{MBS_ERR_NEAR_TARGET,
+                                               "target " + std::to_string(i) + " lies inside the proxy surface of body " +
+                                                   std::to_string(t)};
+                        }
+                    }
+        }
+        const double* dp = in_dev_real(c, pts, (size_t)d * M, "io_pts");
+        const double2* dq = in_dev(c, qhat, (size_t)c->N * nrhs, "io_q");
+        OutBuf ou = out_dev(c, u, (size_t)M * nrhs, "io_u");
+        int ns;
+        int* sb = split_for(c, M, &ns);
+        double2* part = scratch<double2>(c, "part_field", (size_t)ns * nrhs * M);
+        launch_field_f64(glayout(c), c->kappa, M, dp, nrhs, dq, ou.dev, part, ns, sb, c->st);
+        finish_out(c, ou);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_inject_scattering(mbs_ctx* c, int shape, int k, const int* skel, const double* S,
+                                 const double* W) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (shape < 0 || shape >= (int)c->shapes.size() || !c->shapes[shape].used)
+            throw MbsError{MBS_ERR_ARG, "shape not built"};
+        ShapeHost& s = c->shapes[shape];
+        if (k < 1 || k > s.m || !skel || !S) throw MbsError{MBS_ERR_ARG, "bad k / skel / S"};
+        for (int i = 0; i < k; ++i)
+            if (skel[i] < 0 || skel[i] >= s.m) throw MbsError{MBS_ERR_ARG, "skeleton index out of range"};
+        if (!W && (k != s.k || !std::equal(skel, skel + k, s.skel.begin())))
+            throw MbsError{MBS_ERR_ARG, "W is required when the skeleton differs from the built one"};
+        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+        s.k = k;
+        s.skel.assign(skel, skel + k);
+        s.S64 = galloc<double2>(c, (size_t)k * k);
+        s.S32 = galloc<float2>(c, (size_t)k * k);
+        MBS_CUDA_TRY(cudaMemcpy(s.S64, S, (size_t)k * k * sizeof(double2), cudaMemcpyHostToDevice));
+        launch_f64_to_f32(s.S64, s.S32, (int64_t)k * k, c->st);
+        if (W) {
+            s.W = galloc<double2>(c, (size_t)k * s.m);
+            MBS_CUDA_TRY(cudaMemcpy(s.W, W, (size_t)k * s.m * sizeof(double2), cudaMemcpyHostToDevice));
+        } else {
+            s.W = nullptr;
+        }
+        refresh_layout(c);
+        return MBS_OK;
+    });
+}
+
+}  // extern "C"

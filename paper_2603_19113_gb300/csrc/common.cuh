@@ -1,0 +1,121 @@
+// Shared device/host definitions of the multibody scattering library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <string>
+
+#include "../../include/mbs.h"
+
+#define MBS_PI 3.14159265358979323846
+#define MBS_TWO_PI 6.28318530717958647692
+#define MBS_EULER_GAMMA 0.57721566490153286061
+
+// ----------------------------------------------------------------------------
+// complex helpers (interleaved re/im in float2 / double2)
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
+    return make_double2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) {
+    return make_double2(a.x * s, a.y * s);
+}
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ----------------------------------------------------------------------------
+// error reporting
+// ----------------------------------------------------------------------------
+struct MbsError {
+    mbs_status st;
+    std::string msg;
+};
+
+#define MBS_CUDA_TRY(call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            throw MbsError{e_ == cudaErrorMemoryAllocation ? MBS_ERR_NOMEM : MBS_ERR_CUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+        }                                                                               \
+    } while (0)
+
+#define MBS_CHECK_LAUNCH() MBS_CUDA_TRY(cudaGetLastError())
+
+// ----------------------------------------------------------------------------
+// device-side geometry of the skeleton layout, shared by the G_hat kernels
+// ----------------------------------------------------------------------------
+struct GLayout {
+    int dim;
+    int T;                    // bodies
+    int64_t N;                // skeleton points
+    const int* body;          // [N] body id of each skeleton point (sorted)
+    const int64_t* off;       // [T+1] first skeleton point of each body
+    const float* loc32;       // [dim][N] local offsets delta_i = R_tau x_local (FP32)
+    const double* xw64;       // [dim][N] world coordinates (FP64)
+    const float4* pair;       // [T*T] per body pair: D = c_tau - c_sigma, |D| (2D: Dx,Dy,R,phi0; 3D: Dx,Dy,Dz,R)
+    const float* pair_phi0;   // [T*T] 3D only: (kappa R) mod 2 pi
+};
+
+// Launch wrappers (gmatvec.cu)
+void launch_pair_table(int dim, int T, const double* d_centres, double kappa, float4* pair,
+                       float* pair_phi0, cudaStream_t st);
+void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
+                  float2* part, int nsplit, const int* d_split_body, cudaStream_t st);
+void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
+                  double2* part, int nsplit, const int* d_split_body, cudaStream_t st);
+void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
+                      const double2* q, double2* u, double2* part, int nsplit,
+                      const int* d_split_body, cudaStream_t st);
+
+// S application and vector kernels (blas.cu)
+struct SBlocks {
+    int T;
+    const int* k;             // [T] skeleton count per body
+    const int64_t* off;       // [T+1]
+    const double2* const* S64;  // [T] pointer to body's S (k x k column-major), FP64
+    const float2* const* S32;   // [T] same, FP32
+};
+void launch_sapply_f32(const SBlocks& B, int64_t N, int nrhs, const float2* x, const float2* y,
+                       float2* z, int kmax, cudaStream_t st);
+void launch_sapply_f64(const SBlocks& B, int64_t N, int nrhs, const double2* x, const double2* y,
+                       double2* z, int kmax, cudaStream_t st);
+
+// Multi-RHS Krylov kernels: vectors are [nrhs][N]; bases are [j][nrhs][N].
+template <typename V>
+void launch_dots(const V* basis, int nvec, const V* w, int64_t N, int nrhs, double2* out,
+                 double2* scratch, int nblk, cudaStream_t st);
+template <typename V>
+void launch_update(const V* basis, int nvec, const double2* h, V* w, int64_t N, int nrhs,
+                   double sign, cudaStream_t st);
+template <typename V>
+void launch_scale(V* w, const double* inv, V* out, int64_t N, int nrhs, cudaStream_t st);
+void launch_norms64(const double2* x, int64_t N, int nrhs, double* out, double* scratch,
+                    int nblk, cudaStream_t st);
+void launch_f64_to_f32_scaled(const double2* x, const double* scale, float2* y, int64_t N,
+                              int nrhs, cudaStream_t st);
+void launch_axpy_f32_into_f64(const float2* d, const double* scale, double2* x, int64_t N,
+                              int nrhs, cudaStream_t st);
+void launch_sub64(const double2* b, const double2* ax, double2* r, int64_t N, int nrhs,
+                  cudaStream_t st);
+template <typename V>
+void launch_sub(const V* b, const V* ax, V* r, int64_t n, cudaStream_t st);
+void launch_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t st);
+void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st);
+
+int mbs_num_sms();

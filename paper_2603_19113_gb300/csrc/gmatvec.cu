@@ -1,0 +1,403 @@
+// Block-masked all-pairs G_hat matvec and field evaluation.
+//
+// y_i = sum_{j : body(j) != body(i)} phi_kappa(x_hat_i - x_hat_j) q_j for every
+// right-hand side (Sec. 1, eq. Gmtx-entries; the diagonal blocks of G_hat are
+// zero, Sec. 2.2 eq. mbody2), and u(t) = sum_j phi(t - x_hat_j) q_j for
+// arbitrary targets (Sec. 4.1, eq. out_skel).
+//
+// Launch shape: a CTA owns 256 consecutive targets (two per thread) and one
+// contiguous range of source bodies (grid.y = source split).  Sources are
+// staged body by body through shared memory and read as broadcasts; phi is
+// evaluated once per pair and multiplied into every right-hand side held in
+// registers.  Each split writes its own partial sums and a second kernel
+// reduces them in a fixed order, so results do not depend on scheduling.
+//
+// FP32 path (inner solves): coordinates are split as x_hat = c_tau + delta
+// with small local offsets delta.  Per body pair (tau, sigma) a table holds
+// D = c_tau - c_sigma, R = |D| and the phase (kappa R + const) mod 2 pi,
+// computed once in FP64.  Per point pair, with d = delta_i - delta_j,
+//     s = 2 D.d + |d|^2,  r^2 = R^2 + s,  r - R = s / (r + R),
+// so the phase kappa r = kappa R + kappa (r - R) keeps FP32 accuracy even when
+// kappa r is in the thousands.
+#include "bessel.cuh"
+#include "common.cuh"
+
+namespace {
+
+constexpr int TPB = 128;  // threads per CTA
+constexpr int TILE = 2 * TPB;  // targets per CTA
+constexpr int SB = 128;  // sources staged per round
+
+__global__ void pair_table_kernel(int dim, int T, const double* __restrict__ c, double kappa,
+                                  float4* __restrict__ pair, float* __restrict__ phi0) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)T * T) return;
+    const int a = (int)(idx / T), b = (int)(idx % T);
+    const double dx = c[3 * a] - c[3 * b], dy = c[3 * a + 1] - c[3 * b + 1];
+    const double dz = dim == 3 ? c[3 * a + 2] - c[3 * b + 2] : 0.0;
+    const double R = sqrt(dx * dx + dy * dy + dz * dz);
+    if (dim == 2) {
+        const double ph = fmod(kappa * R + 0.25 * MBS_PI, MBS_TWO_PI);
+        pair[idx] = make_float4((float)dx, (float)dy, (float)R, (float)ph);
+    } else {
+        pair[idx] = make_float4((float)dx, (float)dy, (float)dz, (float)R);
+        phi0[idx] = (float)fmod(kappa * R, MBS_TWO_PI);
+    }
+}
+
+// phi for one point pair in FP32 with the body-pair phase split.
+// P = (Dx, Dy, R, phi0) in 2D, (Dx, Dy, Dz, R) in 3D (phi0 passed separately).
+template <int DIM>
+__device__ __forceinline__ float2 pair_phi_f32(const float* di, const float* dj, const float4 P,
+                                               const float phi0, const float kappa,
+                                               const float ampc, const float c2xa, bool act) {
+    const float dx = di[0] - dj[0];
+    const float dy = di[1] - dj[1];
+    float s, R;
+    if (DIM == 2) {
+        s = fmaf(fmaf(2.f, P.x, dx), dx, fmaf(2.f, P.y, dy) * dy);
+        R = P.z;
+    } else {
+        const float dz = di[2] - dj[2];
+        s = fmaf(fmaf(2.f, P.x, dx), dx, fmaf(fmaf(2.f, P.y, dy), dy, fmaf(2.f, P.z, dz) * dz));
+        R = P.w;
+    }
+    float r2 = fmaf(R, R, s);
+    r2 = act ? r2 : 1.f;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    float2 out;
+    if (DIM == 2) {
+        const float x = kappa * r;
+        if (x >= MBS_F32_X3_XA) {
+            const float dr = __fdividef(s, r + R);
+            const float u = fmaf(c2xa, rinv, -1.f);
+            const float f = horner_f32<MBS_F32_X3_DEG>(c_f32_F, u);
+            const float g = horner_f32<MBS_F32_X3_DEG>(c_f32_G, u);
+            float ph = P.w + fmaf(kappa, dr, g);
+            const float n = rintf(ph * 0.159154943091895336f);
+            ph = fmaf(-n, 6.28125f, ph);
+            ph = fmaf(-n, 1.93530717958647692e-3f, ph);
+            float sn, cs;
+            __sincosf(ph, &sn, &cs);
+            const float amp = ampc * f * rsqrtf(r);
+            out = make_float2(amp * cs, amp * sn);
+        } else {
+            out = phi2d_small_f32(x);
+        }
+    } else {
+        const float dr = __fdividef(s, r + R);
+        float ph = fmaf(kappa, dr, phi0);
+        const float n = rintf(ph * 0.159154943091895336f);
+        ph = fmaf(-n, 6.28125f, ph);
+        ph = fmaf(-n, 1.93530717958647692e-3f, ph);
+        float sn, cs;
+        __sincosf(ph, &sn, &cs);
+        const float amp = 0.0795774715459476679f * rinv;  // 1 / (4 pi r)
+        out = make_float2(amp * cs, amp * sn);
+    }
+    return act ? out : make_float2(0.f, 0.f);
+}
+
+template <int DIM, int NR>
+__global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const float kappa,
+                                                    const float ampc, const float c2xa,
+                                                    const int nrhs, const int r0,
+                                                    const float2* __restrict__ q,
+                                                    float2* __restrict__ part,
+                                                    const int* __restrict__ split_body) {
+    __shared__ float s_loc[DIM][SB];
+    __shared__ float2 s_q[SB * NR];
+    const int64_t N = L.N;
+    const int T = L.T;
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * TILE + tid;
+    const int64_t i1 = i0 + TPB;
+    const bool v0 = i0 < N, v1 = i1 < N;
+    const int tb0 = v0 ? L.body[i0] : -1;
+    const int tb1 = v1 ? L.body[i1] : -1;
+    float d0[DIM], d1[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        d0[c] = v0 ? L.loc32[c * N + i0] : 0.f;
+        d1[c] = v1 ? L.loc32[c * N + i1] : 0.f;
+    }
+    float2 a0[NR], a1[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        a0[r] = make_float2(0.f, 0.f);
+        a1[r] = make_float2(0.f, 0.f);
+    }
+    const int sb0 = split_body[blockIdx.y], sb1 = split_body[blockIdx.y + 1];
+    for (int sb = sb0; sb < sb1; ++sb) {
+        const int64_t js = L.off[sb], je = L.off[sb + 1];
+        const bool act0 = v0 && tb0 != sb;
+        const bool act1 = v1 && tb1 != sb;
+        const float4 P0 = act0 ? L.pair[(int64_t)tb0 * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
+        const float4 P1 = act1 ? L.pair[(int64_t)tb1 * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
+        float f00 = 0.f, f01 = 0.f;
+        if (DIM == 3) {
+            f00 = act0 ? L.pair_phi0[(int64_t)tb0 * T + sb] : 0.f;
+            f01 = act1 ? L.pair_phi0[(int64_t)tb1 * T + sb] : 0.f;
+        }
+        for (int64_t jc = js; jc < je; jc += SB) {
+            const int n = (int)min((int64_t)SB, je - jc);
+            __syncthreads();
+            if (tid < n) {
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) s_loc[c][tid] = L.loc32[c * N + jc + tid];
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    s_q[tid * NR + r] =
+                        (r0 + r < nrhs) ? q[(int64_t)(r0 + r) * N + jc + tid] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            if (act0 || act1) {
+#pragma unroll 2
+                for (int jj = 0; jj < n; ++jj) {
+                    float dj[DIM];
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) dj[c] = s_loc[c][jj];
+                    const float2 p0 = pair_phi_f32<DIM>(d0, dj, P0, f00, kappa, ampc, c2xa, act0);
+                    const float2 p1 = pair_phi_f32<DIM>(d1, dj, P1, f01, kappa, ampc, c2xa, act1);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float2 qq = s_q[jj * NR + r];
+                        a0[r].x = fmaf(p0.x, qq.x, fmaf(-p0.y, qq.y, a0[r].x));
+                        a0[r].y = fmaf(p0.x, qq.y, fmaf(p0.y, qq.x, a0[r].y));
+                        a1[r].x = fmaf(p1.x, qq.x, fmaf(-p1.y, qq.y, a1[r].x));
+                        a1[r].y = fmaf(p1.x, qq.y, fmaf(p1.y, qq.x, a1[r].y));
+                    }
+                }
+            }
+        }
+    }
+    float2* out = part + (int64_t)blockIdx.y * nrhs * N;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        if (r0 + r < nrhs) {
+            if (v0) out[(int64_t)(r0 + r) * N + i0] = a0[r];
+            if (v1) out[(int64_t)(r0 + r) * N + i1] = a1[r];
+        }
+    }
+}
+
+// FP64 path: world coordinates, no phase split.  Used for the FP64 operator,
+// the refinement residual and field evaluation (tbody == nullptr: no mask).
+template <int DIM, int NR>
+__global__ void __launch_bounds__(TPB) g_f64_kernel(
+    const int64_t Nt, const double* __restrict__ tgt, const int* __restrict__ tbody,
+    const int64_t Ns, const double* __restrict__ src, const int64_t* __restrict__ soff,
+    const double kappa, const int nrhs, const int r0, const double2* __restrict__ q,
+    double2* __restrict__ part, const int* __restrict__ split_body) {
+    __shared__ double s_x[DIM][SB];
+    __shared__ double2 s_q[SB * NR];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * TILE + tid;
+    const int64_t i1 = i0 + TPB;
+    const bool v0 = i0 < Nt, v1 = i1 < Nt;
+    const int tb0 = (v0 && tbody) ? tbody[i0] : -1;
+    const int tb1 = (v1 && tbody) ? tbody[i1] : -1;
+    double x0[DIM], x1[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        x0[c] = v0 ? tgt[c * Nt + i0] : 0.0;
+        x1[c] = v1 ? tgt[c * Nt + i1] : 0.0;
+    }
+    double2 a0[NR], a1[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        a0[r] = make_double2(0.0, 0.0);
+        a1[r] = make_double2(0.0, 0.0);
+    }
+    const int sb0 = split_body[blockIdx.y], sb1 = split_body[blockIdx.y + 1];
+    for (int sb = sb0; sb < sb1; ++sb) {
+        const int64_t js = soff[sb], je = soff[sb + 1];
+        const bool act0 = v0 && tb0 != sb;
+        const bool act1 = v1 && tb1 != sb;
+        for (int64_t jc = js; jc < je; jc += SB) {
+            const int n = (int)min((int64_t)SB, je - jc);
+            __syncthreads();
+            if (tid < n) {
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) s_x[c][tid] = src[c * Ns + jc + tid];
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    s_q[tid * NR + r] = (r0 + r < nrhs) ? q[(int64_t)(r0 + r) * Ns + jc + tid]
+                                                        : make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+            if (act0 || act1) {
+                for (int jj = 0; jj < n; ++jj) {
+                    double r20 = 0.0, r21 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) {
+                        const double sx = s_x[c][jj];
+                        const double e0 = x0[c] - sx, e1 = x1[c] - sx;
+                        r20 = fma(e0, e0, r20);
+                        r21 = fma(e1, e1, r21);
+                    }
+                    double2 p0 = make_double2(0.0, 0.0), p1 = make_double2(0.0, 0.0);
+                    if (act0) p0 = phi_f64<DIM>(kappa, sqrt(r20));
+                    if (act1) p1 = phi_f64<DIM>(kappa, sqrt(r21));
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const double2 qq = s_q[jj * NR + r];
+                        a0[r].x = fma(p0.x, qq.x, fma(-p0.y, qq.y, a0[r].x));
+                        a0[r].y = fma(p0.x, qq.y, fma(p0.y, qq.x, a0[r].y));
+                        a1[r].x = fma(p1.x, qq.x, fma(-p1.y, qq.y, a1[r].x));
+                        a1[r].y = fma(p1.x, qq.y, fma(p1.y, qq.x, a1[r].y));
+                    }
+                }
+            }
+        }
+    }
+    double2* out = part + (int64_t)blockIdx.y * nrhs * Nt;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        if (r0 + r < nrhs) {
+            if (v0) out[(int64_t)(r0 + r) * Nt + i0] = a0[r];
+            if (v1) out[(int64_t)(r0 + r) * Nt + i1] = a1[r];
+        }
+    }
+}
+
+template <typename V>
+__global__ void reduce_splits_kernel(const V* __restrict__ part, int nsplit, int64_t len,
+                                     V* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    V acc = part[i];
+    for (int s = 1; s < nsplit; ++s) {
+        const V v = part[(int64_t)s * len + i];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    y[i] = acc;
+}
+
+template <int DIM, int NR>
+void launch_f32_chunk(const GLayout& L, float kappa, float ampc, float c2xa, int nrhs, int r0,
+                      const float2* q, float2* part, int nsplit, const int* sb, cudaStream_t st) {
+    dim3 grid((unsigned)((L.N + TILE - 1) / TILE), (unsigned)nsplit);
+    g_f32_kernel<DIM, NR><<<grid, TPB, 0, st>>>(L, kappa, ampc, c2xa, nrhs, r0, q, part, sb);
+}
+
+template <int DIM>
+void launch_f32_dim(const GLayout& L, float kappa, float ampc, float c2xa, int nrhs,
+                    const float2* q, float2* part, int nsplit, const int* sb, cudaStream_t st) {
+    int r0 = 0;
+    while (r0 < nrhs) {
+        const int left = nrhs - r0;
+        if (left >= 16) {
+            launch_f32_chunk<DIM, 16>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            r0 += 16;
+        } else if (left > 4) {
+            launch_f32_chunk<DIM, 8>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            r0 += 8;
+        } else if (left > 2) {
+            launch_f32_chunk<DIM, 4>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            r0 += 4;
+        } else if (left == 2) {
+            launch_f32_chunk<DIM, 2>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            r0 += 2;
+        } else {
+            launch_f32_chunk<DIM, 1>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            r0 += 1;
+        }
+        MBS_CHECK_LAUNCH();
+    }
+}
+
+template <int DIM, int NR>
+void launch_f64_chunk(int64_t Nt, const double* tgt, const int* tbody, int64_t Ns,
+                      const double* src, const int64_t* soff, double kappa, int nrhs, int r0,
+                      const double2* q, double2* part, int nsplit, const int* sb, cudaStream_t st) {
+    dim3 grid((unsigned)((Nt + TILE - 1) / TILE), (unsigned)nsplit);
+    g_f64_kernel<DIM, NR><<<grid, TPB, 0, st>>>(Nt, tgt, tbody, Ns, src, soff, kappa, nrhs, r0, q,
+                                               part, sb);
+}
+
+template <int DIM>
+void launch_f64_dim(int64_t Nt, const double* tgt, const int* tbody, int64_t Ns,
+                    const double* src, const int64_t* soff, double kappa, int nrhs,
+                    const double2* q, double2* part, int nsplit, const int* sb, cudaStream_t st) {
+    int r0 = 0;
+    while (r0 < nrhs) {
+        const int left = nrhs - r0;
+        if (left > 4) {
+            launch_f64_chunk<DIM, 8>(Nt, tgt, tbody, Ns, src, soff, kappa, nrhs, r0, q, part,
+                                     nsplit, sb, st);
+            r0 += 8;
+        } else if (left > 2) {
+            launch_f64_chunk<DIM, 4>(Nt, tgt, tbody, Ns, src, soff, kappa, nrhs, r0, q, part,
+                                     nsplit, sb, st);
+            r0 += 4;
+        } else if (left == 2) {
+            launch_f64_chunk<DIM, 2>(Nt, tgt, tbody, Ns, src, soff, kappa, nrhs, r0, q, part,
+                                     nsplit, sb, st);
+            r0 += 2;
+        } else {
+            launch_f64_chunk<DIM, 1>(Nt, tgt, tbody, Ns, src, soff, kappa, nrhs, r0, q, part,
+                                     nsplit, sb, st);
+            r0 += 1;
+        }
+        MBS_CHECK_LAUNCH();
+    }
+}
+
+}  // namespace
+
+void launch_pair_table(int dim, int T, const double* d_centres, double kappa, float4* pair,
+                       float* pair_phi0, cudaStream_t st) {
+    const int64_t n = (int64_t)T * T;
+    if (n == 0) return;
+    pair_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dim, T, d_centres, kappa, pair,
+                                                                   pair_phi0);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
+                  float2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+    if (L.N == 0 || nrhs == 0) return;
+    const float kf = (float)kappa;
+    const float ampc = (float)(0.25 * sqrt(2.0 / (MBS_PI * kappa)));
+    const float c2xa = (float)(2.0 * MBS_F32_X3_XA / kappa);
+    if (L.dim == 2)
+        launch_f32_dim<2>(L, kf, ampc, c2xa, nrhs, q, part, nsplit, d_split_body, st);
+    else
+        launch_f32_dim<3>(L, kf, ampc, c2xa, nrhs, q, part, nsplit, d_split_body, st);
+    const int64_t len = L.N * nrhs;
+    reduce_splits_kernel<float2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
+                  double2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+    if (L.N == 0 || nrhs == 0) return;
+    if (L.dim == 2)
+        launch_f64_dim<2>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
+                          d_split_body, st);
+    else
+        launch_f64_dim<3>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
+                          d_split_body, st);
+    const int64_t len = L.N * nrhs;
+    reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
+    MBS_CHECK_LAUNCH();
+}
+
+// Field evaluation at arbitrary targets: the FP64 kernel without a body mask.
+void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
+                      const double2* q, double2* u, double2* part, int nsplit,
+                      const int* d_split_body, cudaStream_t st) {
+    if (M == 0 || nrhs == 0) return;
+    if (L.dim == 2)
+        launch_f64_dim<2>(M, tgt, nullptr, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
+                          d_split_body, st);
+    else
+        launch_f64_dim<3>(M, tgt, nullptr, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
+                          d_split_body, st);
+    const int64_t len = M * nrhs;
+    reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, u);
+    MBS_CHECK_LAUNCH();
+}

@@ -1,0 +1,52 @@
+// Job descriptors of the batched S build (one per distinct shape) and of the
+// right-hand-side kernel (one per body).
+#pragma once
+
+#include "common.cuh"
+
+struct SBuildJob {
+    // inputs (device, SoA local coordinates)
+    int m, n, p;
+    const double* x;
+    const double* y;
+    const double* z;
+    int kfix;       // > 0: fixed skeleton count
+    double eps;     // else: relative stopping tolerance
+    // workspace
+    double2* BD;    // p x (m + n), ld p: B | D, factored in place
+    double2* AU;    // m x (n + kcap), ld m: A | U, factored in place (kept: A's reflectors, R_A)
+    double2* W1;    // kcap x max(m, n)
+    double2* W2;    // min(p, m) x n
+    double* nrm2;   // max(m, n)
+    int* permB;     // m
+    double2* diagB; // min(p, m)
+    int* permA;     // n (kept)
+    double2* diagA; // n (kept)
+    // outputs
+    int k;          // skeleton count
+    int rankB;
+    int rankA;
+    double eps_ach;
+    int* skel;      // kcap
+    double2* Zs;    // k x m, ld k (kept)
+    double2* C;     // m x n, ld m (kept)
+    double2* S;     // k x k, ld k (kept)
+};
+
+struct RhsBody {
+    int m, n, k, rankA;
+    int64_t voff;   // first collocation row of this body in v
+    int64_t boff;   // first skeleton row of this body in b
+    const double2* A;      // reflectors + R_A (m x n, ld m)
+    const double2* diagA;
+    const int* permA;
+    const double2* C;      // m x n
+    const double2* Zs;     // k x m
+    const double2* W;      // injected k x m, or nullptr
+};
+
+void launch_sbuild_phase1(int dim, SBuildJob* d_jobs, int njobs, int pmax, double kappa,
+                          double rcond, cudaStream_t st);
+void launch_sbuild_phase2(SBuildJob* d_jobs, int njobs, int mmax, double rcond, cudaStream_t st);
+void launch_rhs(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, const double2* v,
+                int64_t Mtot, double2* b, int64_t N, cudaStream_t st);

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (derivations in the design notes):
+  * FP64 kernels: 1e-12 relative to the largest output entry (rounding of sums
+    of N terms with entries accurate to ~1e-15);
+  * FP32 G_hat: 2e-5 norm-wise (per-entry phi error <= ~1e-6 from the phase
+    split, the fitted modulus/phase and the hardware sine/cosine, with a
+    cancellation allowance for the multi-body sum);
+  * solves: relative scattered-field error <= 1e-9 against the oracle (FP64
+    and mixed precision), <= 1e-10 for FP64 with injected scattering data.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mbs_inputs as mi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_19113_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _nrel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _rand(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def _ctx_with_oracle_S(pkg, wl, **kw):
+    sdata = orc.build_all(wl)
+    ctx = pkg.Context(wl.dim, wl.kappa, **kw)
+    ctx.build_scattering_matrices(wl)
+    for s, sd in enumerate(sdata):
+        if sd is not None:
+            ctx.inject_scattering(s, sd["skel"], sd["S"], sd["W"])
+    lay = orc.layout(wl, sdata)
+    return ctx, sdata, lay
+
+
+# --------------------------------------------------------------------------
+# G_hat matvec (several tiles and a ragged tail; nrhs chunking)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 17])
+def test_G_2d_fp64_and_fp32(pkg, nrhs):
+    wl = mi.tiny_2d(seed=1, T=9, kappa=6.0, ks=(24, 37, 50))
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    assert ctx.N > 256 and ctx.N % 256 != 0
+    q = _rand((ctx.N, nrhs), nrhs)
+    G = orc.G_dense(2, wl.kappa, lay["xhat"], lay["body"])
+    ref = G @ q
+    y64 = ctx.apply_G(q, pkg.PREC_FP64)
+    y32 = ctx.apply_G(q, pkg.PREC_FP32)
+    assert _rel(y64, ref) < 1e-12
+    assert _nrel(y32, ref) < 2e-5
+
+
+def test_G_2d_small_arguments(pkg):
+    """Neighbouring bodies at low kappa put kappa r below 3 and between 3 and
+    16: every branch of the H0 evaluation is exercised."""
+    wl = mi.tiny_2d(seed=2, T=9, kappa=2.0, ks=(30, 41), spacing=2.9)
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    x = wl.kappa * np.linalg.norm(lay["xhat"][:, None] - lay["xhat"][None], axis=2)
+    other = lay["body"][:, None] != lay["body"][None, :]
+    assert x[other].min() < 3.0 and x[other].max() > 16.0
+    q = _rand((ctx.N, 2), 7)
+    ref = orc.G_dense(2, wl.kappa, lay["xhat"], lay["body"]) @ q
+    assert _rel(ctx.apply_G(q, pkg.PREC_FP64), ref) < 1e-12
+    assert _nrel(ctx.apply_G(q, pkg.PREC_FP32), ref) < 2e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_G_3d_fp64_and_fp32(pkg, nrhs):
+    wl = mi.tiny_3d(seed=0, T=5, kappa=3.0, nth=10, nph=14, p=141, k=70)
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    q = _rand((ctx.N, nrhs), 11)
+    ref = orc.G_dense(3, wl.kappa, lay["xhat"], lay["body"]) @ q
+    assert _rel(ctx.apply_G(q, pkg.PREC_FP64), ref) < 1e-12
+    assert _nrel(ctx.apply_G(q, pkg.PREC_FP32), ref) < 2e-5
+
+
+def test_apply_operator_matches_oracle(pkg):
+    wl = mi.config0()
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    q = _rand((ctx.N, 1), 3)
+    ref = orc.apply_operator(wl, sdata, lay, q)
+    assert _rel(ctx.apply_operator(q), ref) < 1e-12
+    ctx.set_options(precision=pkg.PREC_FP32)
+    assert _nrel(ctx.apply_operator(q), ref) < 2e-5
+
+
+def test_G_full_size_config1_sampled_rows(pkg):
+    """The bench workload (1000 bodies, N = 64,000, 8 right-hand sides, kappa = 40)
+    in the bench's launch configuration: 256 sampled rows against the oracle."""
+    wl = mi.config1()
+    ctx = pkg.Context(2, wl.kappa)
+    ctx.build_scattering_matrices(wl)
+    N, off, xyz = ctx.get_layout()
+    assert N == 64000
+    body = np.repeat(np.arange(wl.T), np.diff(off))
+    q = _rand((N, 8), 5)
+    y64 = ctx.apply_G(q, pkg.PREC_FP64)
+    y32 = ctx.apply_G(q, pkg.PREC_FP32)
+    rows = np.random.default_rng(0).choice(N, 256, replace=False)
+    ref = orc.G_rows(2, wl.kappa, xyz, body, q, rows)
+    assert _rel(y64[rows], ref) < 1e-12
+    assert _nrel(y32[rows], ref) < 2e-5
+
+
+# --------------------------------------------------------------------------
+# right-hand side, solve, field
+# --------------------------------------------------------------------------
+def test_injected_solve_fp64_and_mixed_config0(pkg):
+    wl = mi.config0()
+    ref = orc.solve_workload(wl)
+    tg = mi.far_targets(wl, 128, mode="ring")
+    u_ref = orc.field(2, wl.kappa, tg, ref["layout"]["xhat"], ref["q"])
+    for prec, tol in ((pkg.PREC_FP64, 1e-10), (pkg.PREC_MIXED, 1e-9)):
+        ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, precision=prec, tol=1e-12)
+        b = ctx.rhs(ref["v"])
+        b_ref = orc.rhs(wl, sdata, lay, ref["v"], explicit_W=True)
+        assert _rel(b, b_ref) < 1e-12
+        q, info = ctx.solve(ref["b"])
+        assert info["converged"] == 1
+        assert _nrel(q, ref["q"]) < tol
+        u = ctx.evaluate_field(tg, q)
+        assert _rel(u, u_ref) < tol
+
+
+def test_evaluate_field_matches_oracle(pkg):
+    wl = mi.tiny_2d(seed=3, T=7, kappa=5.0)
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    q = _rand((ctx.N, 3), 9)
+    tg = mi.far_targets(wl, 300, mode="gaps", seed=4)
+    ref = orc.field(2, wl.kappa, tg, lay["xhat"], q)
+    assert _rel(ctx.evaluate_field(tg, q), ref) < 1e-12
+
+
+def test_gpu_built_S_single_circle_closed_form(pkg):
+    """GPU S build (pivoted QR, ID, least squares) for one circle: the field
+    matches the separation-of-variables solution and the oracle."""
+    from closed_forms import circle_scattered
+    kappa = 10.0
+    wl = mi.circle_single(kappa, m=128, eps=1e-12, proxy_factor=2.0)
+    ctx = pkg.Context(2, kappa, tol=1e-13)
+    ctx.build_scattering_matrices(wl)
+    info = ctx.get_shape(0)
+    sd = orc.build_all(wl)[0]
+    assert np.array_equal(info["skel"], sd["skel"])
+    v = wl.boundary_data()
+    q = ctx.rhs(v)
+    a = np.linspace(0, 2 * np.pi, 120, endpoint=False) + 0.1
+    tg = 2.7 * np.stack([np.cos(a), np.sin(a)], axis=1)
+    u = ctx.evaluate_field(tg, q)[:, 0]
+    assert _rel(u, circle_scattered(kappa, 1.0, 0.0, tg)) < 1e-9
+    # S itself: the outgoing field of S v_hat outside the proxy
+    qs = info["S"] @ v[info["skel"], 0]
+    us = orc.field(2, kappa, tg, wl.shapes[0].x[info["skel"]], qs)
+    assert _rel(us, circle_scattered(kappa, 1.0, 0.0, tg)) < 1e-9
+
+
+def test_gpu_built_pipeline_three_bodies(pkg):
+    """Full GPU pipeline (S build, right-hand side, FP64 and mixed solves, field)
+    against the oracle on three resolved bodies."""
+    shapes = [mi.shape_2d("star3n", 192, 96, 193, 1.8, eps=1e-12),
+              mi.shape_2d("ellipse", 192, 96, 193, 1.8, eps=1e-12)]
+    centres = np.array([[0.0, 0.0, 0], [4.1, 0.6, 0], [1.2, 4.3, 0]])
+    rots = np.stack([mi.rot2(0.3), mi.rot2(1.9), mi.rot2(-0.8)])
+    dirs = np.array([[1.0, 0, 0], [math.cos(2.0), math.sin(2.0), 0]])
+    wl = mi.Workload("three", 2, 5.0, shapes, np.array([0, 1, 0], np.int32), centres, rots, dirs)
+    ref = orc.solve_workload(wl)
+    tg = mi.far_targets(wl, 128, mode="ring")
+    u_ref = orc.field(2, wl.kappa, tg, ref["layout"]["xhat"], ref["q"])
+    for s in range(2):
+        assert np.array_equal(ref["sdata"][s]["skel"], orc.cpqr_id(ref["sdata"][s]["B"], eps=1e-12)[0])
+    for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
+        ctx = pkg.Context(2, wl.kappa, precision=prec, tol=1e-12)
+        ctx.build_scattering_matrices(wl)
+        for s in range(2):
+            assert np.array_equal(ctx.get_shape(s)["skel"], ref["sdata"][s]["skel"])
+        b = ctx.rhs(ref["v"])
+        q, info = ctx.solve(b)
+        assert info["converged"] == 1
+        u = ctx.evaluate_field(tg, q)
+        assert _rel(u, u_ref) < 1e-9, prec
+
+
+# --------------------------------------------------------------------------
+# errors and degenerate cases
+# --------------------------------------------------------------------------
+def test_error_paths(pkg):
+    wl = mi.config0()
+    ctx = pkg.Context(2, wl.kappa)
+    with pytest.raises(pkg.MbsError) as e:
+        ctx.apply_operator(np.zeros((10, 1)))  # before build
+    assert e.value.status == 8
+    ctx.build_scattering_matrices(wl)
+    with pytest.raises(pkg.MbsError) as e:
+        ctx.evaluate_field(np.array([[0.1, 0.2]]), np.zeros((ctx.N, 1)))
+    assert e.value.status == 7
+    bad = mi.config0()
+    bad.centres[1, :2] = bad.centres[0, :2] + 1.0  # body 1 inside body 0's proxy
+    with pytest.raises(pkg.MbsError) as e:
+        pkg.Context(2, wl.kappa).build_scattering_matrices(bad)
+    assert e.value.status == 2
+
+
+def test_single_body_has_no_coupling(pkg):
+    wl = mi.circle_single(3.0, m=96, eps=1e-10, proxy_factor=2.0)
+    ctx = pkg.Context(2, wl.kappa)
+    ctx.build_scattering_matrices(wl)
+    q = _rand((ctx.N, 2), 1)
+    assert np.all(ctx.apply_G(q) == 0)
+    b = ctx.rhs(wl.boundary_data())
+    x, info = ctx.solve(b)
+    assert _rel(x, b) < 1e-14
