@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of the multibody scattering hot path on GB300.
+
+One step = the whole path on the 2D workload of 1000 bodies (circle /
+3-star / ellipse, N = 64,000 skeleton points, kappa = 40, 8 plane waves):
+scattering-matrix build on the device, layout, right-hand side, the
+mixed-precision solve (FP32 GMRES inside FP64 iterative refinement) to a
+relative residual of 1e-11, and the scattered field at 4096 far targets.
+
+value = G_hat pair-interactions per second over the step (one pair = one
+phi evaluation with its multiply-add into all 8 right-hand sides; every
+operator application and the field evaluation count).  Under torchrun each
+rank runs an independent replica (the path is not sharded across GPUs).
+
+--impl reference times the CPU oracle (numpy/scipy FP64) on a bounded
+sample of the same workload with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ĝ pair-interactions/s; time-to-1e-9 mixed vs FP64 on GB300; served p50/p99"
+UNIT = "pair-interactions/s"
+WORKLOAD = ("2D sound-soft, 1000 bodies (circle, 3-star, ellipse 1:0.6; radius 1) on a jittered "
+            "32x32 lattice in a 100x100 box, random rotations, kappa=40, m=128 n=64 k=64 p=129 "
+            "per body (N=64,000), 8 plane waves; mixed FP32/FP64-IR solve to rel. residual 1e-11")
+FLOPS_PER_PAIR_2D = lambda nrhs: 35 + 8 * nrhs  # noqa: E731  (convention)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mbs", choices=["mbs", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-11)
+    ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--targets", type=int, default=4096)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 time-to-solution solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--kernel", choices=["g32", "g64"], default=None,
+                    help="only apply G_hat (FP32 or FP64) to 8 random vectors, steps times "
+                         "(for profiling the dominant kernel); prints per-launch times")
+    return ap.parse_args()
+
+
+def run_kernel_only(a):
+    import numpy as np
+    import torch
+
+    import mbs_inputs as mi
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_19113_gb300 as pkg
+
+    wl = mi.config1()
+    stream = torch.cuda.current_stream()
+    ctx = pkg.Context(2, wl.kappa, stream=stream.cuda_stream)
+    ctx.build_scattering_matrices(wl)
+    q = torch.randn(wl.nrhs, ctx.N, dtype=torch.complex128, device="cuda").T
+    prec = pkg.PREC_FP32 if a.kernel == "g32" else pkg.PREC_FP64
+    for _ in range(a.warmup):
+        ctx.apply_G(q, prec)
+    ctx.profile(True)
+    ctx.kernel_times()
+    for _ in range(a.steps):
+        ctx.apply_G(q, prec)
+    kt = ctx.kernel_times()
+    print(json.dumps({"kernel": a.kernel, "N": ctx.N, "nrhs": wl.nrhs, **kt}), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_rows(args):
+    import numpy as np
+    import oracle as orc
+    xyz, body, q, rows, kappa = args
+    t0 = time.perf_counter()
+    orc.G_rows(2, kappa, xyz, body, q, rows)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_setup(seed=0):
+    import numpy as np
+    import mbs_inputs as mi
+    import oracle as orc
+    wl = mi.config1(seed=seed)
+    sdata = orc.build_all(wl)
+    lay = orc.layout(wl, sdata)
+    rng = np.random.default_rng(1)
+    N = lay["xhat"].shape[0]
+    q = rng.normal(size=(N, wl.nrhs)) + 1j * rng.normal(size=(N, wl.nrhs))
+    return wl, lay, q
+
+
+def oracle_pairs_per_s(pool, nproc, wl, lay, q, rows_total, seed=2):
+    """Time the oracle's G_hat rows on a random sample of target rows, spread
+    over a process pool; returns (pairs/s, seconds, rows)."""
+    import numpy as np
+    N = lay["xhat"].shape[0]
+    rows = np.sort(np.random.default_rng(seed).choice(N, rows_total, replace=False))
+    chunks = np.array_split(rows, nproc * 2)
+    t0 = time.perf_counter()
+    list(pool.map(_oracle_rows, [(lay["xhat"], lay["body"], q, c, wl.kappa) for c in chunks]))
+    dt = time.perf_counter() - t0
+    pairs = 0
+    for r in rows:
+        pairs += N - int(np.sum(lay["body"] == lay["body"][r]))
+    return pairs / dt, dt, rows_total
+
+
+def make_pool():
+    import multiprocessing as mp
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(n), n
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    pool, nproc = make_pool()
+    wl, lay, q = oracle_sample_setup()
+    rows = max(64, 16 * nproc)
+    for _ in range(a.warmup):
+        oracle_pairs_per_s(pool, nproc, wl, lay, q, rows, seed=10)
+    t0 = time.perf_counter()
+    rates = []
+    for s in range(a.steps):
+        r, dt, _ = oracle_pairs_per_s(pool, nproc, wl, lay, q, rows, seed=20 + s)
+        rates.append(r)
+    total = time.perf_counter() - t0
+    pool.close()
+    value = statistics.mean(rates)
+    sample = f"oracle G_hat rows: {rows} random target rows x 64,000 sources x 8 RHS per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "CPU oracle (numpy/scipy)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_mbs(a, ws, rank, local):
+    pool = None
+    nproc = 0
+    if rank == 0 and not a.no_cpu:
+        pool, nproc = make_pool()  # spawn before any CUDA work
+    import numpy as np
+    import torch
+
+    import mbs_inputs as mi
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_19113_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = mi.config1(seed=rank)
+    v_host = wl.boundary_data()
+    tg_host = mi.far_targets(wl, a.targets, mode="ring")
+    M = tg_host.shape[0]
+    nrhs = wl.nrhs
+    # device-resident inputs (column-major (rows, nrhs) complex128; targets (M, 2))
+    v_dev = torch.from_numpy(np.ascontiguousarray(v_host.T)).to(dev).T
+    tg_dev = torch.from_numpy(np.ascontiguousarray(tg_host.T)).to(dev).T
+    # pinned host inputs for the end-to-end measurement
+    v_pin = torch.from_numpy(np.ascontiguousarray(v_host.T)).pin_memory().T
+    tg_pin = torch.from_numpy(np.ascontiguousarray(tg_host.T)).pin_memory().T
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=1e-6, restart=a.restart,
+                max_iter=50000, max_sweeps=12, stream=stream.cuda_stream)
+    ctx = pkg.Context(2, wl.kappa, **opts)
+
+    def step(v, tg):
+        ctx.build_scattering_matrices(wl)
+        b = ctx.rhs(v)
+        q, info = ctx.solve(b)
+        u = ctx.evaluate_field(tg, q)
+        return info, u
+
+    ctx.build_scattering_matrices(wl)
+    N = ctx.N
+    _, off, _ = ctx.get_layout()
+    kb = np.diff(off)
+    pairs_mv = N * N - int(np.sum(kb.astype(np.int64) ** 2))
+    for _ in range(a.warmup):
+        flush.zero_()
+        info, _ = step(v_dev, tg_dev)
+
+    # ---- timed region: device-resident inputs ----
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    ctx.kernel_times()
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    sampler.start()
+    l0 = pkg.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pairs = 0
+    infos = []
+    for _ in range(a.steps):
+        flush.zero_()
+        info, u = step(v_dev, tg_dev)
+        infos.append(info)
+        pairs += (info["matvecs_fp32"] + info["matvecs_fp64"]) * pairs_mv + M * N
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    launches = pkg.launch_count() - l0
+    clocks = sampler.stop()
+    kt = ctx.kernel_times()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1)
+    ms_max = reduce_max(ms, ws, dev)
+    pairs_all = reduce_sum(pairs, ws, dev)
+    value = pairs_all / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e_pairs = 0
+    h2d = d2h = 0
+    for _ in range(a.steps):
+        flush.zero_()
+        ctx.build_scattering_matrices(wl)
+        b = ctx.rhs(v_pin)                 # H2D v, D2H b
+        q, info = ctx.solve(b)             # H2D b (and x0), D2H q
+        u = ctx.evaluate_field(tg_pin, q)  # H2D targets and q, D2H u
+        e_pairs += (info["matvecs_fp32"] + info["matvecs_fp64"]) * pairs_mv + M * N
+        h2d += v_pin.numel() * 16 + 2 * b.numel() * 16 + q.numel() * 16 + tg_pin.numel() * 8
+        d2h += b.numel() * 16 + q.numel() * 16 + u.numel() * 16
+    torch.cuda.synchronize(dev)
+    e_dt = reduce_max(time.perf_counter() - t0, ws, dev)
+    e_value = reduce_sum(e_pairs, ws, dev) / e_dt
+
+    # ---- FP64 path: time to the same tolerance (one solve) ----
+    t2s = {"mixed_s": statistics.mean(i["seconds"] for i in infos),
+           "mixed_inner_iterations": infos[-1]["inner_iterations"],
+           "mixed_sweeps": infos[-1]["sweeps"], "mixed_rel_residual": infos[-1]["rel_residual"],
+           "tol": a.tol}
+    if not a.no_fp64 and rank == 0:
+        ctx64 = pkg.Context(2, wl.kappa, precision=pkg.PREC_FP64, tol=a.tol, restart=a.restart,
+                            max_iter=50000, stream=stream.cuda_stream)
+        ctx64.build_scattering_matrices(wl)
+        b64 = ctx64.rhs(v_dev)
+        q64, i64 = ctx64.solve(b64, raise_on_noconv=False)
+        t2s.update({"fp64_s": i64["seconds"], "fp64_iterations": i64["inner_iterations"],
+                    "fp64_rel_residual": i64["rel_residual"], "fp64_converged": i64["converged"]})
+        q_mix, _ = ctx.solve(ctx.rhs(v_dev))
+        u64 = ctx64.evaluate_field(tg_dev, q64)
+        umx = ctx.evaluate_field(tg_dev, q_mix)
+        t2s["mixed_vs_fp64_field_rel_err"] = float((u64 - umx).abs().max() / u64.abs().max())
+        ctx64.close()
+
+    # ---- roofline of the dominant kernel (FP32 G_hat) ----
+    flops_launch = pairs_mv * FLOPS_PER_PAIR_2D(nrhs)
+    avg_ms = kt["g32_ms"] / max(1, kt["g32_launches"])
+    achieved = flops_launch / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "g_f32_kernel<2,8>", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None, "avg_launch_ms": avg_ms, "launches": kt["g32_launches"],
+                "flops_per_launch": flops_launch,
+                "peak_note": "FP32 SIMT peak from unit counts: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    share = kt["g32_ms"] / ms if ms > 0 else None
+
+    cpu = None
+    if pool is not None:
+        import oracle  # noqa: F401  (test infrastructure: CPU baseline leg only)
+        wlo, lay, qo = oracle_sample_setup()
+        rows = max(64, 32 * nproc)
+        rate, dt, _ = oracle_pairs_per_s(pool, nproc, wlo, lay, qo, rows)
+        pool.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": nproc, "kind": "oracle",
+               "sample": f"oracle G_hat rows: {rows} random target rows x 64,000 sources x 8 RHS "
+                         f"({dt:.1f} s wall on {nproc} processes)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "pairs_per_matvec": pairs_mv, "nrhs": nrhs,
+                       "field_targets": M, "l2": "256 MiB buffer written before every step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // a.steps,
+                    "d2h_bytes_per_step": d2h // a.steps},
+            "roofline": roofline,
+            "g32_time_share": share,
+            "time_to_solution": t2s,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_setup()
+    if a.kernel:
+        run_kernel_only(a)
+    elif a.impl == "reference":
+        run_reference(a, ws, rank)
+    else:
+        run_mbs(a, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

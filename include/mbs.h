@@ -200,6 +200,22 @@ mbs_status mbs_inject_scattering(mbs_ctx* ctx, int shape, int k, const int* skel
  * count, out[4] SM clock kHz.  Runs on the current device. */
 mbs_status mbs_measure_peaks(double* out);
 
+/* ---- instrumentation ---- */
+
+/* Number of CUDA kernels the library has launched in this process (all
+ * contexts), for launch accounting around a timed region. */
+int64_t mbs_launch_count(void);
+
+/* enable != 0: bracket every G_hat kernel launch of this context with CUDA
+ * events on the context's stream (the split reduction is not included). */
+mbs_status mbs_profile(mbs_ctx* ctx, int enable);
+
+/* Sum the bracketed G_hat kernel times since the last call and reset:
+ * out[0] = total ms of FP32 G_hat launches, out[1] = their count,
+ * out[2] = total ms of FP64 G_hat launches, out[3] = their count.
+ * Synchronises the context's stream. */
+mbs_status mbs_kernel_times(mbs_ctx* ctx, double* out);
+
 /* ---- serving: continuous batching of independent solves (one GPU) ---- */
 typedef struct mbs_server mbs_server;
 

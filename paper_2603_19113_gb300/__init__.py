@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     MbsError,
     Server,
     default_options,
+    launch_count,
     measure_peaks,
     shapes_bodies_from_workload,
 )

@@ -80,6 +80,9 @@ SIGNATURES = {
     "mbs_evaluate_field": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P]),
     "mbs_inject_scattering": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), _P, _P]),
     "mbs_measure_peaks": (C.c_int, [_D]),
+    "mbs_launch_count": (C.c_int64, []),
+    "mbs_profile": (C.c_int, [_P, C.c_int]),
+    "mbs_kernel_times": (C.c_int, [_P, _D]),
     "mbs_serve_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(_P)]),
     "mbs_serve_submit": (C.c_int, [_P, C.POINTER(mbs_request), C.POINTER(C.c_int64)]),
     "mbs_serve_poll": (C.c_int, [_P, C.c_int64, C.POINTER(mbs_request_result), _P]),

@@ -76,7 +76,9 @@ class _Arg:
 
 def _out_like(arg: _Arg, rows: int):
     if arg.torch:
-        t = torch.empty((arg.nrhs, rows), dtype=torch.complex128, device=arg.keep.device).T
+        dev = arg.keep.device
+        pin = dev.type == "cpu" and arg.keep.is_pinned()
+        t = torch.empty((arg.nrhs, rows), dtype=torch.complex128, device=dev, pin_memory=pin).T
         return t, C.c_void_p(t.data_ptr())
     buf = np.empty((arg.nrhs, rows), dtype=np.complex128)
     return buf, C.c_void_p(buf.ctypes.data)
@@ -217,7 +219,10 @@ class Context:
         a = _Arg(b, self.N)
         if x0 is None:
             if a.torch:
-                x = torch.zeros((a.nrhs, self.N), dtype=torch.complex128, device=a.keep.device).T
+                dev = a.keep.device
+                pin = dev.type == "cpu" and a.keep.is_pinned()
+                x = torch.zeros((a.nrhs, self.N), dtype=torch.complex128, device=dev,
+                                pin_memory=pin).T
                 xp = C.c_void_p(x.data_ptr())
             else:
                 x = np.zeros((a.nrhs, self.N), dtype=np.complex128)
@@ -237,7 +242,9 @@ class Context:
     def evaluate_field(self, pts, qhat):
         a = _Arg(qhat, self.N)
         if _is_torch(pts):
-            P = pts.to(torch.float64).T.contiguous()
+            P = pts.to(torch.float64)
+            P = P if P.T.is_contiguous() else P.T.contiguous().T
+            P = P.T
             pp = C.c_void_p(P.data_ptr())
             M = pts.shape[0]
         else:
@@ -258,6 +265,26 @@ class Context:
         N = C.c_int64()
         self._check(_lib().mbs_get_layout(self._h, C.byref(N), None, None))
         self.N = int(N.value)
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libmbs.so so far in this process."""
+    return int(_lib().mbs_launch_count())
+
+
+def _ctx_profile(self, enable: bool = True):
+    self._check(_lib().mbs_profile(self._h, 1 if enable else 0))
+
+
+def _ctx_kernel_times(self) -> dict:
+    out = (C.c_double * 4)()
+    self._check(_lib().mbs_kernel_times(self._h, out))
+    return {"g32_ms": out[0], "g32_launches": int(out[1]), "g64_ms": out[2],
+            "g64_launches": int(out[3])}
+
+
+Context.profile = _ctx_profile
+Context.kernel_times = _ctx_kernel_times
 
 
 def measure_peaks() -> dict:

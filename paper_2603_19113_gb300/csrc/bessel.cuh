@@ -14,6 +14,8 @@
 #include "bessel_coeffs.h"
 #include "common.cuh"
 
+__device__ __constant__ float c_f32_8F[MBS_F32_X8_DEG + 1] = MBS_F32_X8_F;
+__device__ __constant__ float c_f32_8G[MBS_F32_X8_DEG + 1] = MBS_F32_X8_G;
 __device__ __constant__ float c_f32_F[MBS_F32_X3_DEG + 1] = MBS_F32_X3_F;
 __device__ __constant__ float c_f32_G[MBS_F32_X3_DEG + 1] = MBS_F32_X3_G;
 __device__ __constant__ double c_f64_4F[MBS_F64_X4_DEG + 1] = MBS_F64_X4_F;

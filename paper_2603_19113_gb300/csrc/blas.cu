@@ -81,35 +81,61 @@ __global__ void __launch_bounds__(256) sapply_kernel(const SBlocks B, const int6
     }
 }
 
-// partial[(i*nrhs + r) * nblk + blk] = sum over the block's slice of conj(basis_i,r) . w_r
+constexpr int DOT_E = 8;  // w elements cached per thread: a block covers <= 256 * DOT_E rows
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// partial[(i*nrhs + r) * nblk + blk] = sum over the block's slice of conj(basis_{i,r}) . w_r
+// for every i < nvec.  The block keeps its slice of w_r in registers and walks
+// the basis vectors; per-thread sums are in the vector's precision, the
+// cross-warp sums in FP64.
 template <typename V>
 __global__ void __launch_bounds__(256) dots_kernel(const V* __restrict__ basis, const int nvec,
                                                    const V* __restrict__ w, const int64_t N,
                                                    const int nrhs, double2* __restrict__ partial,
                                                    const int nblk) {
-    const int ir = blockIdx.y;  // i * nrhs + r
-    const int r = ir % nrhs;
-    const V* __restrict__ vb = basis + (int64_t)ir * N;
-    const V* __restrict__ wr = w + (int64_t)r * N;
-    double sx = 0.0, sy = 0.0;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (int64_t)gridDim.x * blockDim.x) {
-        const V a = vb[n], b = wr[n];
-        sx += (double)a.x * b.x + (double)a.y * b.y;
-        sy += (double)a.x * b.y - (double)a.y * b.x;
+    using T = typename Acc<V>::T;
+    extern __shared__ double2 s_acc[];
+    const int r = blockIdx.y, blk = blockIdx.x;
+    const int64_t chunk = (N + nblk - 1) / nblk;
+    const int64_t n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s_acc[i] = make_double2(0.0, 0.0);
+    V wv[DOT_E];
+#pragma unroll
+    for (int e = 0; e < DOT_E; ++e) {
+        const int64_t n = n0 + threadIdx.x + (int64_t)e * blockDim.x;
+        V z;
+        z.x = z.y = T(0);
+        wv[e] = n < n1 ? w[(int64_t)r * N + n] : z;
     }
-    __shared__ double rx[256], ry[256];
-    rx[threadIdx.x] = sx;
-    ry[threadIdx.x] = sy;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            rx[threadIdx.x] += rx[threadIdx.x + s];
-            ry[threadIdx.x] += ry[threadIdx.x + s];
+    for (int i = 0; i < nvec; ++i) {
+        const V* __restrict__ vb = basis + ((int64_t)i * nrhs + r) * N;
+        T sx = T(0), sy = T(0);
+#pragma unroll
+        for (int e = 0; e < DOT_E; ++e) {
+            const int64_t n = n0 + threadIdx.x + (int64_t)e * blockDim.x;
+            if (n < n1) {
+                const V a = vb[n];
+                sx = fma(a.x, wv[e].x, fma(a.y, wv[e].y, sx));
+                sy = fma(a.x, wv[e].y, fma(-a.y, wv[e].x, sy));
+            }
         }
-        __syncthreads();
+        sx = warp_sum_t(sx);
+        sy = warp_sum_t(sy);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_acc[i].x, (double)sx);
+            atomicAdd(&s_acc[i].y, (double)sy);
+        }
     }
-    if (threadIdx.x == 0) partial[(int64_t)ir * nblk + blockIdx.x] = make_double2(rx[0], ry[0]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x)
+        partial[((int64_t)i * nrhs + r) * nblk + blk] = s_acc[i];
 }
 
 __global__ void dots_finish_kernel(const double2* __restrict__ partial, int count, int nblk,
@@ -128,19 +154,29 @@ __global__ void __launch_bounds__(256) update_kernel(const V* __restrict__ basis
                                                      V* __restrict__ w, const int64_t N,
                                                      const int nrhs, const double sign) {
     using T = typename Acc<V>::T;
+    extern __shared__ unsigned char upd_raw[];
+    V* s_h = reinterpret_cast<V*>(upd_raw);
     const int r = blockIdx.y;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        const double2 c = h[i * nrhs + r];
+        V cv;
+        cv.x = (T)(sign * c.x);
+        cv.y = (T)(sign * c.y);
+        s_h[i] = cv;
+    }
+    __syncthreads();
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (int64_t)gridDim.x * blockDim.x) {
-        double ax = 0.0, ay = 0.0;
+        V o = w[(int64_t)r * N + n];
+        T ax = o.x, ay = o.y;
         for (int i = 0; i < nvec; ++i) {
             const V v = basis[((int64_t)i * nrhs + r) * N + n];
-            const double2 c = h[i * nrhs + r];
-            ax += (double)v.x * c.x - (double)v.y * c.y;
-            ay += (double)v.x * c.y + (double)v.y * c.x;
+            const V c = s_h[i];
+            ax = fma(v.x, c.x, fma(-v.y, c.y, ax));
+            ay = fma(v.x, c.y, fma(v.y, c.x, ay));
         }
-        V o = w[(int64_t)r * N + n];
-        o.x = (T)((double)o.x + sign * ax);
-        o.y = (T)((double)o.y + sign * ay);
+        o.x = ax;
+        o.y = ay;
         w[(int64_t)r * N + n] = o;
     }
 }
@@ -272,8 +308,14 @@ template <typename V>
 void launch_dots(const V* basis, int nvec, const V* w, int64_t N, int nrhs, double2* out,
                  double2* scratch, int nblk, cudaStream_t st) {
     if (nvec == 0) return;
-    dim3 g((unsigned)nblk, (unsigned)(nvec * nrhs));
-    dots_kernel<V><<<g, 256, 0, st>>>(basis, nvec, w, N, nrhs, scratch, nblk);
+    if ((int64_t)nblk * 256 * DOT_E < N)
+        throw MbsError{MBS_ERR_ARG, "launch_dots: too few blocks for the vector length"};
+    dim3 g((unsigned)nblk, (unsigned)nrhs);
+    const size_t sm = (size_t)nvec * sizeof(double2);
+    if (sm > 48 * 1024)
+        MBS_CUDA_TRY(cudaFuncSetAttribute(dots_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm));
+    dots_kernel<V><<<g, 256, sm, st>>>(basis, nvec, w, N, nrhs, scratch, nblk);
     MBS_CHECK_LAUNCH();
     dots_finish_kernel<<<nblocks(nvec * nrhs, 128), 128, 0, st>>>(scratch, nvec * nrhs, nblk, out);
     MBS_CHECK_LAUNCH();
@@ -285,7 +327,11 @@ void launch_update(const V* basis, int nvec, const double2* h, V* w, int64_t N, 
     if (nvec == 0) return;
     const unsigned gx = (unsigned)std::min<int64_t>((N + 255) / 256, 4 * mbs_num_sms());
     dim3 g(gx, (unsigned)nrhs);
-    update_kernel<V><<<g, 256, 0, st>>>(basis, nvec, h, w, N, nrhs, sign);
+    const size_t sm = (size_t)nvec * sizeof(V);
+    if (sm > 48 * 1024)
+        MBS_CUDA_TRY(cudaFuncSetAttribute(update_kernel<V>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    update_kernel<V><<<g, 256, sm, st>>>(basis, nvec, h, w, N, nrhs, sign);
     MBS_CHECK_LAUNCH();
 }
 

@@ -1,6 +1,7 @@
 // C ABI of the multibody scattering library: context, S build driver,
 // layout, right-hand side, operator, GMRES / GMRES-IR solve and field
 // evaluation.  See include/mbs.h for the contract of every call.
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -12,6 +13,8 @@
 
 #include "common.cuh"
 #include "sbuild.cuh"
+
+std::atomic<long long> g_mbs_launches{0};
 
 namespace {
 
@@ -73,6 +76,11 @@ struct mbs_ctx {
     const float2** d_S32p = nullptr;
     RhsBody* d_rhsb = nullptr;
     std::map<std::pair<int64_t, int>, int*> split_cache;  // (targets, nsplit) -> split_body
+
+    // live timing of the G_hat kernels (mbs_profile)
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev32, ev64;
 
     // allocations
     std::vector<void*> geom_allocs;  // freed on rebuild
@@ -261,18 +269,41 @@ SBlocks sblocks(mbs_ctx* c) {
     return B;
 }
 
+cudaEvent_t take_event(mbs_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    MBS_CUDA_TRY(cudaEventCreate(&e));
+    return e;
+}
+
 // y = G_hat x (FP32)
 void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
     int ns;
     int* sb = split_for(c, c->N, &ns);
     float2* part = scratch<float2>(c, "part32", (size_t)ns * nrhs * c->N);
-    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        c->ev32.emplace_back(e0, e1);
+    }
+    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st, e0, e1);
 }
 void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
     int ns;
     int* sb = split_for(c, c->N, &ns);
     double2* part = scratch<double2>(c, "part64", (size_t)ns * nrhs * c->N);
-    launch_G_f64(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        c->ev64.emplace_back(e0, e1);
+    }
+    launch_G_f64(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st, e0, e1);
 }
 
 // out = x + S G_hat x
@@ -298,22 +329,25 @@ void apply_op<double2>(mbs_ctx* c, int nrhs, const double2* x, double2* out) {
     op64(c, nrhs, x, out);
 }
 
-int dot_blocks(int64_t N) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((N + 1023) / 1024, 2LL * mbs_num_sms()));
+// Blocks per RHS of the dot-product kernel: each block covers at most 2048
+// rows (its slice of w stays in registers); aim at ~4 blocks per SM overall.
+int dot_blocks(int64_t N, int nrhs) {
+    const int64_t minb = (N + 2047) / 2048;
+    const int64_t want = (4LL * mbs_num_sms() + nrhs - 1) / nrhs;
+    const int64_t maxb = (N + 255) / 256;
+    return (int)std::max<int64_t>(1, std::max(minb, std::min(want, maxb)));
 }
 
 // Per-RHS 2-norms of a [nrhs][N] vector block (host result).
 template <typename V>
 std::vector<double> norms(mbs_ctx* c, const V* x, int nrhs) {
-    const int nb = dot_blocks(c->N);
+    const int nb = dot_blocks(c->N, nrhs);
     double2* d = scratch<double2>(c, "nrm_out", nrhs);
     double2* sc = scratch<double2>(c, "nrm_sc", (size_t)nrhs * nb);
     std::vector<double2> h(nrhs);
     // the "basis" is x itself with one vector per RHS: dots(x_r, x_r) for each r
     std::vector<double> out(nrhs);
-    for (int r = 0; r < nrhs; ++r) {
-        launch_dots<V>(x + (int64_t)r * c->N, 1, x + (int64_t)r * c->N, c->N, 1, d + r, sc, nb, c->st);
-    }
+    launch_dots<V>(x, 1, x, c->N, nrhs, d, sc, nb, c->st);
     MBS_CUDA_TRY(cudaMemcpyAsync(h.data(), d, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
     MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
     for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, h[r].x));
@@ -344,7 +378,7 @@ GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol
                           (size_t)(restart + 1) * NV);
     V* w = scratch<V>(c, std::string("gm_w") + (sizeof(V) == 8 ? "32" : "64"), NV);
     V* r = scratch<V>(c, std::string("gm_r") + (sizeof(V) == 8 ? "32" : "64"), NV);
-    const int nb = dot_blocks(N);
+    const int nb = dot_blocks(N, nrhs);
     double2* d_h = scratch<double2>(c, "gm_h", (size_t)(2 * (restart + 1) + 1) * nrhs);
     double2* d_sc = scratch<double2>(c, "gm_sc", (size_t)(restart + 1) * nrhs * nb);
     double* d_inv = scratch<double>(c, "gm_inv", nrhs);
@@ -365,9 +399,22 @@ GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol
     std::vector<double2> hh((size_t)(2 * (restart + 1) + 1) * nrhs);
     std::vector<double> inv(nrhs);
     std::vector<int> msteps(nrhs), frozen(nrhs);
+    double prev_worst = 1e300;
     while (true) {
         std::vector<double> beta = norms<V>(c, r, nrhs);
         bool all = true;
+        double worst = 0.0;
+        for (int q = 0; q < nrhs; ++q) {
+            const double rel = bn[q] > 0 ? beta[q] / bn[q] : 0.0;
+            worst = std::max(worst, rel);
+        }
+        // a restart cycle that did not reduce the worst true residual by 10 %
+        // has hit the precision floor of this arithmetic: stop
+        if (worst > 0.9 * prev_worst && worst > tol) {
+            for (int q = 0; q < nrhs; ++q) S.relres[q] = bn[q] > 0 ? beta[q] / bn[q] : 0.0;
+            break;
+        }
+        prev_worst = worst;
         for (int q = 0; q < nrhs; ++q) {
             const double rel = bn[q] > 0 ? beta[q] / bn[q] : 0.0;
             S.relres[q] = rel;
@@ -397,8 +444,7 @@ GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol
             launch_update<V>(basis, j + 1, h1, w, N, nrhs, -1.0, c->st);
             launch_dots<V>(basis, j + 1, w, N, nrhs, h2, d_sc, nb, c->st);
             launch_update<V>(basis, j + 1, h2, w, N, nrhs, -1.0, c->st);
-            for (int q = 0; q < nrhs; ++q)
-                launch_dots<V>(w + (size_t)q * N, 1, w + (size_t)q * N, N, 1, hn + q, d_sc, nb, c->st);
+            launch_dots<V>(w, 1, w, N, nrhs, hn, d_sc, nb, c->st);
             MBS_CUDA_TRY(cudaMemcpyAsync(hh.data(), d_h, hh.size() * sizeof(double2),
                                          cudaMemcpyDeviceToHost, c->st));
             MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -899,11 +945,55 @@ mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** o
     return MBS_OK;
 }
 
+int64_t mbs_launch_count(void) { return (int64_t)g_mbs_launches.load(); }
+
+mbs_status mbs_profile(mbs_ctx* c, int enable) {
+    return guarded(c, [&]() {
+        c->profile = enable != 0;
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_kernel_times(mbs_ctx* c, double* out) {
+    return guarded(c, [&]() {
+        if (!out) throw MbsError{MBS_ERR_ARG, "null output"};
+        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+        double t[2] = {0.0, 0.0};
+        size_t n[2] = {c->ev32.size(), c->ev64.size()};
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* lists[2] = {&c->ev32, &c->ev64};
+        for (int a = 0; a < 2; ++a) {
+            for (auto& pr : *lists[a]) {
+                float ms = 0.f;
+                MBS_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+                t[a] += ms;
+                c->ev_pool.push_back(pr.first);
+                c->ev_pool.push_back(pr.second);
+            }
+            lists[a]->clear();
+        }
+        out[0] = t[0];
+        out[1] = (double)n[0];
+        out[2] = t[1];
+        out[3] = (double)n[1];
+        return MBS_OK;
+    });
+}
+
 void mbs_destroy(mbs_ctx* c) {
     if (!c) return;
     {
         std::lock_guard<std::mutex> g(c->mu);
         free_geometry(c);
+        if (c->st) cudaStreamSynchronize(c->st);
+        for (auto& pr : c->ev32) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        for (auto& pr : c->ev64) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
         for (auto& kv : c->bufs) dfree(c, kv.second.p);
         c->bufs.clear();
         if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -1062,6 +1152,7 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
                 launch_sub<double2>(db, t64, r64, (int64_t)n, c->st);
             }
             std::vector<double> sc(nrhs);
+            double prev = 1e300;
             while (true) {
                 const std::vector<double> rn = norms<double2>(c, r64, nrhs);
                 relmax = 0.0;
@@ -1076,6 +1167,8 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
                     break;
                 }
                 if (inf.sweeps >= o.max_sweeps || inf.inner_iterations >= o.max_iter) break;
+                if (relmax > 0.5 * prev) break;  // refinement no longer contracts
+                prev = relmax;
                 for (int q = 0; q < nrhs; ++q) {
                     const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
                     sc[q] = (rel > o.tol && rn[q] > 0) ? 1.0 / rn[q] : 0.0;
@@ -1101,7 +1194,10 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
         inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (info) *info = inf;
         if (!conv) {
-            c->err = "solve did not reach tol (relative residual " + std::to_string(relmax) + ")";
+            char msg[160];
+            std::snprintf(msg, sizeof(msg), "solve did not reach tol %.3e (relative residual %.3e)", o.tol,
+                          relmax);
+            c->err = msg;
             return MBS_ERR_NOCONV;
         }
         return MBS_OK;

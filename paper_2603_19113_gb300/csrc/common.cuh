@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
 #include <string>
@@ -55,7 +56,14 @@ struct MbsError {
         }                                                                               \
     } while (0)
 
-#define MBS_CHECK_LAUNCH() MBS_CUDA_TRY(cudaGetLastError())
+// Every kernel launch of the library is followed by MBS_CHECK_LAUNCH(), which
+// also counts it (mbs_launch_count).
+extern std::atomic<long long> g_mbs_launches;
+#define MBS_CHECK_LAUNCH()                                    \
+    do {                                                      \
+        g_mbs_launches.fetch_add(1, std::memory_order_relaxed); \
+        MBS_CUDA_TRY(cudaGetLastError());                     \
+    } while (0)
 
 // ----------------------------------------------------------------------------
 // device-side geometry of the skeleton layout, shared by the G_hat kernels
@@ -75,10 +83,14 @@ struct GLayout {
 // Launch wrappers (gmatvec.cu)
 void launch_pair_table(int dim, int T, const double* d_centres, double kappa, float4* pair,
                        float* pair_phi0, cudaStream_t st);
+// ev0/ev1 (nullable) are recorded on st around the G_hat kernel launches
+// (not the split reduction), for live timing of the dominant kernel.
 void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
-                  float2* part, int nsplit, const int* d_split_body, cudaStream_t st);
+                  float2* part, int nsplit, const int* d_split_body, cudaStream_t st,
+                  cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
-                  double2* part, int nsplit, const int* d_split_body, cudaStream_t st);
+                  double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
+                  cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
                       const double2* q, double2* u, double2* part, int nsplit,
                       const int* d_split_body, cudaStream_t st);

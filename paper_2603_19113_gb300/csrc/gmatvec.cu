@@ -45,12 +45,46 @@ __global__ void pair_table_kernel(int dim, int T, const double* __restrict__ c, 
     }
 }
 
+struct F32Const {
+    float kappa;  // wavenumber
+    float ampc;   // (1/4) sqrt(2 / (pi kappa))
+    float c8;     // 2 * 8 / kappa  (u = c8 / r - 1 for the x >= 8 fit)
+    float c3;     // 2 * 3 / kappa
+};
+
+// exp(i ph) reduced to [-pi, pi] by a two-constant Cody-Waite step (6.28125 is
+// exact in 8 bits, so n * 6.28125 is exact for the |n| < 2^16 that occur).
+__device__ __forceinline__ float2 expi_f32(float ph) {
+    const float n = rintf(ph * 0.159154943091895336f);
+    ph = fmaf(-n, 6.28125f, ph);
+    ph = fmaf(-n, 1.93530717958647692e-3f, ph);
+    float sn, cs;
+    __sincosf(ph, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+// (i/4) H0(kappa r) for kappa r >= XA from the modulus/phase fit, with the
+// phase kappa r + pi/4 + g split as phi0 + kappa (r - R) + g.
+template <int DEG>
+__device__ __forceinline__ float2 far_phi_f32(const float* cf, const float* cg, float c2xa,
+                                              float rinv, float r, float s, float R, float phi0,
+                                              const F32Const& K) {
+    const float dr = __fdividef(s, r + R);
+    const float u = fmaf(c2xa, rinv, -1.f);
+    const float f = horner_f32<DEG>(cf, u);
+    const float g = horner_f32<DEG>(cg, u);
+    const float2 e = expi_f32(phi0 + fmaf(K.kappa, dr, g));
+    const float amp = K.ampc * f * rsqrtf(r);
+    return make_float2(amp * e.x, amp * e.y);
+}
+
 // phi for one point pair in FP32 with the body-pair phase split.
-// P = (Dx, Dy, R, phi0) in 2D, (Dx, Dy, Dz, R) in 3D (phi0 passed separately).
+// P = (Dx, Dy, R, phi0) in 2D, (Dx, Dy, Dz, R) in 3D (phi0 passed separately);
+// R2 = R * R.  The caller never passes a pair of the same body.
 template <int DIM>
 __device__ __forceinline__ float2 pair_phi_f32(const float* di, const float* dj, const float4 P,
-                                               const float phi0, const float kappa,
-                                               const float ampc, const float c2xa, bool act) {
+                                               const float R2, const float phi0,
+                                               const F32Const& K) {
     const float dx = di[0] - dj[0];
     const float dy = di[1] - dj[1];
     float s, R;
@@ -62,46 +96,60 @@ __device__ __forceinline__ float2 pair_phi_f32(const float* di, const float* dj,
         s = fmaf(fmaf(2.f, P.x, dx), dx, fmaf(fmaf(2.f, P.y, dy), dy, fmaf(2.f, P.z, dz) * dz));
         R = P.w;
     }
-    float r2 = fmaf(R, R, s);
-    r2 = act ? r2 : 1.f;
+    const float r2 = R2 + s;
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    float2 out;
     if (DIM == 2) {
-        const float x = kappa * r;
-        if (x >= MBS_F32_X3_XA) {
-            const float dr = __fdividef(s, r + R);
-            const float u = fmaf(c2xa, rinv, -1.f);
-            const float f = horner_f32<MBS_F32_X3_DEG>(c_f32_F, u);
-            const float g = horner_f32<MBS_F32_X3_DEG>(c_f32_G, u);
-            float ph = P.w + fmaf(kappa, dr, g);
-            const float n = rintf(ph * 0.159154943091895336f);
-            ph = fmaf(-n, 6.28125f, ph);
-            ph = fmaf(-n, 1.93530717958647692e-3f, ph);
-            float sn, cs;
-            __sincosf(ph, &sn, &cs);
-            const float amp = ampc * f * rsqrtf(r);
-            out = make_float2(amp * cs, amp * sn);
-        } else {
-            out = phi2d_small_f32(x);
-        }
+        const float x = K.kappa * r;
+        if (x >= MBS_F32_X8_XA)
+            return far_phi_f32<MBS_F32_X8_DEG>(c_f32_8F, c_f32_8G, K.c8, rinv, r, s, R, P.w, K);
+        if (x >= MBS_F32_X3_XA)
+            return far_phi_f32<MBS_F32_X3_DEG>(c_f32_F, c_f32_G, K.c3, rinv, r, s, R, P.w, K);
+        return phi2d_small_f32(x);
     } else {
         const float dr = __fdividef(s, r + R);
-        float ph = fmaf(kappa, dr, phi0);
-        const float n = rintf(ph * 0.159154943091895336f);
-        ph = fmaf(-n, 6.28125f, ph);
-        ph = fmaf(-n, 1.93530717958647692e-3f, ph);
-        float sn, cs;
-        __sincosf(ph, &sn, &cs);
+        const float2 e = expi_f32(fmaf(K.kappa, dr, phi0));
         const float amp = 0.0795774715459476679f * rinv;  // 1 / (4 pi r)
-        out = make_float2(amp * cs, amp * sn);
+        return make_float2(amp * e.x, amp * e.y);
     }
-    return act ? out : make_float2(0.f, 0.f);
 }
 
-template <int DIM, int NR>
-__global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const float kappa,
-                                                    const float ampc, const float c2xa,
+// Sources jj < n of the staged chunk against this thread's TPT targets.
+// MASKED: some targets are inactive (own body or past the end) and skip phi.
+template <int DIM, int NR, int TPT, bool MASKED>
+__device__ __forceinline__ void pair_loop_f32(const int n, const float (*s_loc)[SB],
+                                              const float2* s_q, const float (&d)[TPT][DIM],
+                                              const float4 (&P)[TPT], const float (&R2)[TPT],
+                                              const float (&f0)[TPT], const bool (&act)[TPT],
+                                              const F32Const& K, float2 (&a)[TPT][NR]) {
+#pragma unroll 2
+    for (int jj = 0; jj < n; ++jj) {
+        float dj[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dj[c] = s_loc[c][jj];
+        float2 p[TPT];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            if (MASKED)
+                p[t] = act[t] ? pair_phi_f32<DIM>(d[t], dj, P[t], R2[t], f0[t], K) : make_float2(0.f, 0.f);
+            else
+                p[t] = pair_phi_f32<DIM>(d[t], dj, P[t], R2[t], f0[t], K);
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const float2 qq = s_q[jj * NR + r];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                a[t][r].x = fmaf(p[t].x, qq.x, fmaf(-p[t].y, qq.y, a[t][r].x));
+                a[t][r].y = fmaf(p[t].x, qq.y, fmaf(p[t].y, qq.x, a[t][r].y));
+            }
+        }
+    }
+}
+
+// Targets of thread tid: tile + tid + t * TPB for t < TPT (coalesced loads/stores).
+template <int DIM, int NR, int TPT>
+__global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const F32Const K,
                                                     const int nrhs, const int r0,
                                                     const float2* __restrict__ q,
                                                     float2* __restrict__ part,
@@ -111,34 +159,37 @@ __global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const float
     const int64_t N = L.N;
     const int T = L.T;
     const int tid = threadIdx.x;
-    const int64_t i0 = (int64_t)blockIdx.x * TILE + tid;
-    const int64_t i1 = i0 + TPB;
-    const bool v0 = i0 < N, v1 = i1 < N;
-    const int tb0 = v0 ? L.body[i0] : -1;
-    const int tb1 = v1 ? L.body[i1] : -1;
-    float d0[DIM], d1[DIM];
+    const int64_t base = (int64_t)blockIdx.x * (TPB * TPT) + tid;
+    bool valid[TPT];
+    int tb[TPT];
+    float d[TPT][DIM];
+    float2 a[TPT][NR];
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-        d0[c] = v0 ? L.loc32[c * N + i0] : 0.f;
-        d1[c] = v1 ? L.loc32[c * N + i1] : 0.f;
-    }
-    float2 a0[NR], a1[NR];
+    for (int t = 0; t < TPT; ++t) {
+        const int64_t i = base + (int64_t)t * TPB;
+        valid[t] = i < N;
+        tb[t] = valid[t] ? L.body[i] : -1;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        a0[r] = make_float2(0.f, 0.f);
-        a1[r] = make_float2(0.f, 0.f);
+        for (int c = 0; c < DIM; ++c) d[t][c] = valid[t] ? L.loc32[c * N + i] : 0.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a[t][r] = make_float2(0.f, 0.f);
     }
     const int sb0 = split_body[blockIdx.y], sb1 = split_body[blockIdx.y + 1];
     for (int sb = sb0; sb < sb1; ++sb) {
         const int64_t js = L.off[sb], je = L.off[sb + 1];
-        const bool act0 = v0 && tb0 != sb;
-        const bool act1 = v1 && tb1 != sb;
-        const float4 P0 = act0 ? L.pair[(int64_t)tb0 * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
-        const float4 P1 = act1 ? L.pair[(int64_t)tb1 * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
-        float f00 = 0.f, f01 = 0.f;
-        if (DIM == 3) {
-            f00 = act0 ? L.pair_phi0[(int64_t)tb0 * T + sb] : 0.f;
-            f01 = act1 ? L.pair_phi0[(int64_t)tb1 * T + sb] : 0.f;
+        bool act[TPT];
+        float4 P[TPT];
+        float R2[TPT], f0[TPT];
+        bool all = true, any = false;
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            act[t] = valid[t] && tb[t] != sb;  // zero diagonal blocks of G_hat
+            all = all && act[t];
+            any = any || act[t];
+            P[t] = act[t] ? L.pair[(int64_t)tb[t] * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
+            f0[t] = (DIM == 3 && act[t]) ? L.pair_phi0[(int64_t)tb[t] * T + sb] : 0.f;
+            const float R = DIM == 2 ? P[t].z : P[t].w;
+            R2[t] = R * R;
         }
         for (int64_t jc = js; jc < je; jc += SB) {
             const int n = (int)min((int64_t)SB, je - jc);
@@ -152,32 +203,19 @@ __global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const float
                         (r0 + r < nrhs) ? q[(int64_t)(r0 + r) * N + jc + tid] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            if (act0 || act1) {
-#pragma unroll 2
-                for (int jj = 0; jj < n; ++jj) {
-                    float dj[DIM];
-#pragma unroll
-                    for (int c = 0; c < DIM; ++c) dj[c] = s_loc[c][jj];
-                    const float2 p0 = pair_phi_f32<DIM>(d0, dj, P0, f00, kappa, ampc, c2xa, act0);
-                    const float2 p1 = pair_phi_f32<DIM>(d1, dj, P1, f01, kappa, ampc, c2xa, act1);
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const float2 qq = s_q[jj * NR + r];
-                        a0[r].x = fmaf(p0.x, qq.x, fmaf(-p0.y, qq.y, a0[r].x));
-                        a0[r].y = fmaf(p0.x, qq.y, fmaf(p0.y, qq.x, a0[r].y));
-                        a1[r].x = fmaf(p1.x, qq.x, fmaf(-p1.y, qq.y, a1[r].x));
-                        a1[r].y = fmaf(p1.x, qq.y, fmaf(p1.y, qq.x, a1[r].y));
-                    }
-                }
-            }
+            if (all)
+                pair_loop_f32<DIM, NR, TPT, false>(n, s_loc, s_q, d, P, R2, f0, act, K, a);
+            else if (any)
+                pair_loop_f32<DIM, NR, TPT, true>(n, s_loc, s_q, d, P, R2, f0, act, K, a);
         }
     }
     float2* out = part + (int64_t)blockIdx.y * nrhs * N;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         if (r0 + r < nrhs) {
-            if (v0) out[(int64_t)(r0 + r) * N + i0] = a0[r];
-            if (v1) out[(int64_t)(r0 + r) * N + i1] = a1[r];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t)
+                if (valid[t]) out[(int64_t)(r0 + r) * N + base + (int64_t)t * TPB] = a[t][r];
         }
     }
 }
@@ -276,33 +314,42 @@ __global__ void reduce_splits_kernel(const V* __restrict__ part, int nsplit, int
     y[i] = acc;
 }
 
+// Targets per thread of the FP32 kernel: 4 up to 8 right-hand sides (the
+// staged sources are shared by more pairs), 2 for 16 (register budget).
+template <int NR>
+constexpr int f32_tpt() {
+    return NR >= 16 ? 2 : 4;
+}
+
 template <int DIM, int NR>
-void launch_f32_chunk(const GLayout& L, float kappa, float ampc, float c2xa, int nrhs, int r0,
+void launch_f32_chunk(const GLayout& L, const F32Const& K, int nrhs, int r0,
                       const float2* q, float2* part, int nsplit, const int* sb, cudaStream_t st) {
-    dim3 grid((unsigned)((L.N + TILE - 1) / TILE), (unsigned)nsplit);
-    g_f32_kernel<DIM, NR><<<grid, TPB, 0, st>>>(L, kappa, ampc, c2xa, nrhs, r0, q, part, sb);
+    constexpr int TPT = f32_tpt<NR>();
+    constexpr int tile = TPB * TPT;
+    dim3 grid((unsigned)((L.N + tile - 1) / tile), (unsigned)nsplit);
+    g_f32_kernel<DIM, NR, TPT><<<grid, TPB, 0, st>>>(L, K, nrhs, r0, q, part, sb);
 }
 
 template <int DIM>
-void launch_f32_dim(const GLayout& L, float kappa, float ampc, float c2xa, int nrhs,
+void launch_f32_dim(const GLayout& L, const F32Const& K, int nrhs,
                     const float2* q, float2* part, int nsplit, const int* sb, cudaStream_t st) {
     int r0 = 0;
     while (r0 < nrhs) {
         const int left = nrhs - r0;
         if (left >= 16) {
-            launch_f32_chunk<DIM, 16>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            launch_f32_chunk<DIM, 16>(L, K, nrhs, r0, q, part, nsplit, sb, st);
             r0 += 16;
         } else if (left > 4) {
-            launch_f32_chunk<DIM, 8>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            launch_f32_chunk<DIM, 8>(L, K, nrhs, r0, q, part, nsplit, sb, st);
             r0 += 8;
         } else if (left > 2) {
-            launch_f32_chunk<DIM, 4>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            launch_f32_chunk<DIM, 4>(L, K, nrhs, r0, q, part, nsplit, sb, st);
             r0 += 4;
         } else if (left == 2) {
-            launch_f32_chunk<DIM, 2>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            launch_f32_chunk<DIM, 2>(L, K, nrhs, r0, q, part, nsplit, sb, st);
             r0 += 2;
         } else {
-            launch_f32_chunk<DIM, 1>(L, kappa, ampc, c2xa, nrhs, r0, q, part, nsplit, sb, st);
+            launch_f32_chunk<DIM, 1>(L, K, nrhs, r0, q, part, nsplit, sb, st);
             r0 += 1;
         }
         MBS_CHECK_LAUNCH();
@@ -358,29 +405,37 @@ void launch_pair_table(int dim, int T, const double* d_centres, double kappa, fl
 }
 
 void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
-                  float2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+                  float2* part, int nsplit, const int* d_split_body, cudaStream_t st,
+                  cudaEvent_t ev0, cudaEvent_t ev1) {
     if (L.N == 0 || nrhs == 0) return;
-    const float kf = (float)kappa;
-    const float ampc = (float)(0.25 * sqrt(2.0 / (MBS_PI * kappa)));
-    const float c2xa = (float)(2.0 * MBS_F32_X3_XA / kappa);
+    F32Const K;
+    K.kappa = (float)kappa;
+    K.ampc = (float)(0.25 * sqrt(2.0 / (MBS_PI * kappa)));
+    K.c8 = (float)(2.0 * MBS_F32_X8_XA / kappa);
+    K.c3 = (float)(2.0 * MBS_F32_X3_XA / kappa);
+    if (ev0) MBS_CUDA_TRY(cudaEventRecord(ev0, st));
     if (L.dim == 2)
-        launch_f32_dim<2>(L, kf, ampc, c2xa, nrhs, q, part, nsplit, d_split_body, st);
+        launch_f32_dim<2>(L, K, nrhs, q, part, nsplit, d_split_body, st);
     else
-        launch_f32_dim<3>(L, kf, ampc, c2xa, nrhs, q, part, nsplit, d_split_body, st);
+        launch_f32_dim<3>(L, K, nrhs, q, part, nsplit, d_split_body, st);
+    if (ev1) MBS_CUDA_TRY(cudaEventRecord(ev1, st));
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<float2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
 }
 
 void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
-                  double2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+                  double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
+                  cudaEvent_t ev0, cudaEvent_t ev1) {
     if (L.N == 0 || nrhs == 0) return;
+    if (ev0) MBS_CUDA_TRY(cudaEventRecord(ev0, st));
     if (L.dim == 2)
         launch_f64_dim<2>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
     else
         launch_f64_dim<3>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
+    if (ev1) MBS_CUDA_TRY(cudaEventRecord(ev1, st));
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
