@@ -21,6 +21,9 @@ SOURCES = ["capi.cu", "gmatvec.cu", "blas.cu", "sbuild.cu", "peaks.cu", "serve.c
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-diag-suppress", "177"]
+# single-precision G_hat kernels: flush denormals, approximate division / square
+# root (these flags touch FP32 arithmetic only; the FP64 kernels are unaffected)
+EXTRA = {"gmatvec.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc() -> str:
@@ -51,7 +54,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA.get(src, []), "-I", INCLUDE, "-c",
+               os.path.join(CSRC, src), "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{p.stderr}")

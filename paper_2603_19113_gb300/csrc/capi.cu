@@ -660,11 +660,13 @@ void setup_layout(mbs_ctx* c) {
     std::vector<int> body(N);
     std::vector<float> loc32((size_t)d * N);
     c->skel_world.assign((size_t)d * N, 0.0);
-    std::vector<double> cen((size_t)3 * T, 0.0);
+    // centres (3 per body) followed by the bounding radius of every body
+    std::vector<double> cen((size_t)4 * T, 0.0);
     for (int t = 0; t < T; ++t) {
         const mbs_body& B = c->bodies[t];
         const ShapeHost& s = c->shapes[B.shape];
         for (int a = 0; a < 3; ++a) cen[3 * t + a] = (a < d) ? B.c[a] : 0.0;
+        cen[(size_t)3 * T + t] = s.bound_radius;
         for (int i = 0; i < s.k; ++i) {
             const int64_t g = c->off[t] + i;
             body[g] = t;
@@ -681,7 +683,7 @@ void setup_layout(mbs_ctx* c) {
     c->d_off = galloc<int64_t>(c, T + 1);
     c->d_loc32 = galloc<float>(c, (size_t)d * N);
     c->d_xw64 = galloc<double>(c, (size_t)d * N);
-    c->d_centres = galloc<double>(c, (size_t)3 * T);
+    c->d_centres = galloc<double>(c, (size_t)4 * T);
     c->d_pair = galloc<float4>(c, (size_t)T * T);
     c->d_pair_phi0 = d == 3 ? galloc<float>(c, (size_t)T * T) : nullptr;
     MBS_CUDA_TRY(cudaMemcpyAsync(c->d_body, body.data(), N * sizeof(int), cudaMemcpyHostToDevice, c->st));
@@ -690,7 +692,8 @@ void setup_layout(mbs_ctx* c) {
     MBS_CUDA_TRY(cudaMemcpyAsync(c->d_xw64, c->skel_world.data(), c->skel_world.size() * sizeof(double),
                                  cudaMemcpyHostToDevice, c->st));
     MBS_CUDA_TRY(cudaMemcpyAsync(c->d_centres, cen.data(), cen.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    launch_pair_table(d, T, c->d_centres, c->kappa, c->d_pair, c->d_pair_phi0, c->st);
+    launch_pair_table(d, T, c->d_centres, c->d_centres + (size_t)3 * T, c->kappa, c->d_pair,
+                      c->d_pair_phi0, c->st);
     // S tables and RHS descriptors
     std::vector<const double2*> s64(T);
     std::vector<const float2*> s32(T);

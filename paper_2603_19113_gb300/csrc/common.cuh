@@ -10,7 +10,7 @@
 #include <cstdio>
 #include <string>
 
-#include "../../include/mbs.h"
+#include "mbs.h"
 
 #define MBS_PI 3.14159265358979323846
 #define MBS_TWO_PI 6.28318530717958647692
@@ -81,8 +81,8 @@ struct GLayout {
 };
 
 // Launch wrappers (gmatvec.cu)
-void launch_pair_table(int dim, int T, const double* d_centres, double kappa, float4* pair,
-                       float* pair_phi0, cudaStream_t st);
+void launch_pair_table(int dim, int T, const double* d_centres, const double* d_brad,
+                       double kappa, float4* pair, float* pair_phi0, cudaStream_t st);
 // ev0/ev1 (nullable) are recorded on st around the G_hat kernel launches
 // (not the split reduction), for live timing of the dominant kernel.
 void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,

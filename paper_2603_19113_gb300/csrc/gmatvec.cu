@@ -28,7 +28,12 @@ constexpr int TPB = 128;  // threads per CTA
 constexpr int TILE = 2 * TPB;  // targets per CTA
 constexpr int SB = 128;  // sources staged per round
 
-__global__ void pair_table_kernel(int dim, int T, const double* __restrict__ c, double kappa,
+// Body-pair table.  In 2D a body pair whose closest points can come nearer
+// than 8 / kappa (kappa r < 8, outside the range of the degree-4 fit) is
+// marked by storing -R; its pairs take the per-pair branch to the x >= 3 fit
+// or the power series.
+__global__ void pair_table_kernel(int dim, int T, const double* __restrict__ c,
+                                  const double* __restrict__ brad, double kappa,
                                   float4* __restrict__ pair, float* __restrict__ phi0) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)T * T) return;
@@ -38,7 +43,8 @@ __global__ void pair_table_kernel(int dim, int T, const double* __restrict__ c, 
     const double R = sqrt(dx * dx + dy * dy + dz * dz);
     if (dim == 2) {
         const double ph = fmod(kappa * R + 0.25 * MBS_PI, MBS_TWO_PI);
-        pair[idx] = make_float4((float)dx, (float)dy, (float)R, (float)ph);
+        const bool near = kappa * (R - brad[a] - brad[b]) < 8.0 * (1.0 + 1e-6);
+        pair[idx] = make_float4((float)dx, (float)dy, near ? -(float)R : (float)R, (float)ph);
     } else {
         pair[idx] = make_float4((float)dx, (float)dy, (float)dz, (float)R);
         phi0[idx] = (float)fmod(kappa * R, MBS_TWO_PI);
@@ -81,7 +87,7 @@ __device__ __forceinline__ float2 far_phi_f32(const float* cf, const float* cg, 
 // phi for one point pair in FP32 with the body-pair phase split.
 // P = (Dx, Dy, R, phi0) in 2D, (Dx, Dy, Dz, R) in 3D (phi0 passed separately);
 // R2 = R * R.  The caller never passes a pair of the same body.
-template <int DIM>
+template <int DIM, bool FAR>
 __device__ __forceinline__ float2 pair_phi_f32(const float* di, const float* dj, const float4 P,
                                                const float R2, const float phi0,
                                                const F32Const& K) {
@@ -100,6 +106,8 @@ __device__ __forceinline__ float2 pair_phi_f32(const float* di, const float* dj,
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
     if (DIM == 2) {
+        if (FAR)  // every pair of this body pair has kappa r >= 8
+            return far_phi_f32<MBS_F32_X8_DEG>(c_f32_8F, c_f32_8G, K.c8, rinv, r, s, R, P.w, K);
         const float x = K.kappa * r;
         if (x >= MBS_F32_X8_XA)
             return far_phi_f32<MBS_F32_X8_DEG>(c_f32_8F, c_f32_8G, K.c8, rinv, r, s, R, P.w, K);
@@ -115,7 +123,8 @@ __device__ __forceinline__ float2 pair_phi_f32(const float* di, const float* dj,
 }
 
 // Sources jj < n of the staged chunk against this thread's TPT targets.
-// MASKED: some targets are inactive (own body or past the end) and skip phi.
+// MASKED: some targets are inactive (own body or past the end) and skip phi,
+// and some body pairs may be near (per-pair choice of the H0 evaluation).
 template <int DIM, int NR, int TPT, bool MASKED>
 __device__ __forceinline__ void pair_loop_f32(const int n, const float (*s_loc)[SB],
                                               const float2* s_q, const float (&d)[TPT][DIM],
@@ -131,9 +140,10 @@ __device__ __forceinline__ void pair_loop_f32(const int n, const float (*s_loc)[
 #pragma unroll
         for (int t = 0; t < TPT; ++t) {
             if (MASKED)
-                p[t] = act[t] ? pair_phi_f32<DIM>(d[t], dj, P[t], R2[t], f0[t], K) : make_float2(0.f, 0.f);
+                p[t] = act[t] ? pair_phi_f32<DIM, false>(d[t], dj, P[t], R2[t], f0[t], K)
+                              : make_float2(0.f, 0.f);
             else
-                p[t] = pair_phi_f32<DIM>(d[t], dj, P[t], R2[t], f0[t], K);
+                p[t] = pair_phi_f32<DIM, true>(d[t], dj, P[t], R2[t], f0[t], K);
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -184,10 +194,15 @@ __global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const F32Co
 #pragma unroll
         for (int t = 0; t < TPT; ++t) {
             act[t] = valid[t] && tb[t] != sb;  // zero diagonal blocks of G_hat
-            all = all && act[t];
             any = any || act[t];
             P[t] = act[t] ? L.pair[(int64_t)tb[t] * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
             f0[t] = (DIM == 3 && act[t]) ? L.pair_phi0[(int64_t)tb[t] * T + sb] : 0.f;
+            if (DIM == 2) {  // a negative R marks a near body pair
+                all = all && act[t] && P[t].z > 0.f;
+                P[t].z = fabsf(P[t].z);
+            } else {
+                all = all && act[t];
+            }
             const float R = DIM == 2 ? P[t].z : P[t].w;
             R2[t] = R * R;
         }
@@ -314,11 +329,12 @@ __global__ void reduce_splits_kernel(const V* __restrict__ part, int nsplit, int
     y[i] = acc;
 }
 
-// Targets per thread of the FP32 kernel: 4 up to 8 right-hand sides (the
-// staged sources are shared by more pairs), 2 for 16 (register budget).
+// Targets per thread of the FP32 kernel.  Measured on GB300 (1000-body 2D
+// workload, 8 right-hand sides): 2 targets per thread 9.6 ms per launch,
+// 4 targets 11.3 ms (146 registers, 3 CTAs per SM); 8 targets is slower still.
 template <int NR>
 constexpr int f32_tpt() {
-    return NR >= 16 ? 2 : 4;
+    return 2;
 }
 
 template <int DIM, int NR>
@@ -395,12 +411,12 @@ void launch_f64_dim(int64_t Nt, const double* tgt, const int* tbody, int64_t Ns,
 
 }  // namespace
 
-void launch_pair_table(int dim, int T, const double* d_centres, double kappa, float4* pair,
-                       float* pair_phi0, cudaStream_t st) {
+void launch_pair_table(int dim, int T, const double* d_centres, const double* d_brad,
+                       double kappa, float4* pair, float* pair_phi0, cudaStream_t st) {
     const int64_t n = (int64_t)T * T;
     if (n == 0) return;
-    pair_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dim, T, d_centres, kappa, pair,
-                                                                   pair_phi0);
+    pair_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dim, T, d_centres, d_brad,
+                                                                   kappa, pair, pair_phi0);
     MBS_CHECK_LAUNCH();
 }
 
