@@ -200,6 +200,30 @@ mbs_status mbs_inject_scattering(mbs_ctx* ctx, int shape, int k, const int* skel
  * count, out[4] SM clock kHz.  Runs on the current device. */
 mbs_status mbs_measure_peaks(double* out);
 
+/*
+ * y = G_hat q in FP64 without allocating device memory (the paper has no
+ * counterpart: this is an interface for callers that must not allocate once
+ * they run, e.g. applications that hand out all GPU memory from their own
+ * fixed pool, or real-time loops where a cudaMalloc that may synchronise the
+ * device is not allowed).  No context is needed; every array is a device
+ * pointer owned by the caller:
+ *   body_offsets  T + 1 int64, first skeleton point of each body (sorted by body),
+ *   body          N int32, body index of each point,
+ *   xw            dim * N doubles, world coordinates, SoA,
+ *   q, y          N x nrhs complex (interleaved, column-major).
+ * Work is queued on `stream` (NULL = legacy default stream) and the call
+ * returns without waiting.  Scratch lives in one static 64 MiB device array
+ * per GPU that loads the library, held until the process exits, so
+ * N * nrhs must not exceed 4,194,272 (else MBS_ERR_ARG, nothing launched).
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture); calls that overlap on the GPU share the array
+ * and race.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: MBS_ERR_ARG (sizes, non-device pointers), MBS_ERR_CUDA.
+ */
+mbs_status mbs_apply_G_noalloc(int dim, double kappa, int64_t N, int T, const int64_t* body_offsets,
+                               const int* body, const double* xw, int nrhs, const double* q,
+                               double* y, void* stream);
+
 /* ---- instrumentation ---- */
 
 /* Number of CUDA kernels the library has launched in this process (all

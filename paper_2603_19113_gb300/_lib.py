@@ -80,6 +80,8 @@ SIGNATURES = {
     "mbs_evaluate_field": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P]),
     "mbs_inject_scattering": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), _P, _P]),
     "mbs_measure_peaks": (C.c_int, [_D]),
+    "mbs_apply_G_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_int64, C.c_int, _P, _P, _P,
+                                      C.c_int, _P, _P, _P]),
     "mbs_launch_count": (C.c_int64, []),
     "mbs_profile": (C.c_int, [_P, C.c_int]),
     "mbs_kernel_times": (C.c_int, [_P, _D]),

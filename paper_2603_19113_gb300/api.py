@@ -267,6 +267,27 @@ class Context:
         self.N = int(N.value)
 
 
+def apply_G_noalloc(dim: int, kappa: float, body_offsets, body, xw, q, y, stream=None) -> None:
+    """mbs_apply_G_noalloc: y = G_hat q (FP64) with no device allocation.
+
+    Every argument is a CUDA tensor owned by the caller: body_offsets (T+1,)
+    int64, body (N,) int32, xw (dim, N) float64 SoA, q and y (N, nrhs)
+    complex128 with column-major layout (``torch.empty(nrhs, N).T``).  The
+    work is queued on `stream` (a torch.cuda.Stream or None)."""
+    N = int(body.shape[0])
+    T = int(body_offsets.shape[0]) - 1
+    nrhs = int(q.shape[1]) if q.dim() == 2 else 1
+    for t in (q, y):
+        if not (t.dim() == 1 or t.T.is_contiguous()):
+            raise ValueError("q and y must be column-major (rows, nrhs)")
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    st = _lib().mbs_apply_G_noalloc(dim, kappa, N, T, C.c_void_p(body_offsets.data_ptr()),
+                                    C.c_void_p(body.data_ptr()), C.c_void_p(xw.data_ptr()), nrhs,
+                                    C.c_void_p(q.data_ptr()), C.c_void_p(y.data_ptr()), s)
+    if st != L.MBS_OK:
+        raise MbsError(st, "mbs_apply_G_noalloc")
+
+
 def launch_count() -> int:
     """Kernel launches issued by libmbs.so so far in this process."""
     return int(_lib().mbs_launch_count())
