@@ -75,6 +75,7 @@ typedef struct mbs_options {
     void* stream;        /* cudaStream_t to run on, or NULL for a stream the context creates */
     size_t hbm_budget;   /* bytes of device memory the context may hold (0 = no cap) */
     int tile_override;   /* 0 = tuned launch shape; >0 forces the source-split count of G_hat */
+    int block_krylov;    /* 1 (default): several right-hand sides share one block Krylov space; 0: independent GMRES in lockstep */
 } mbs_options;
 
 typedef struct mbs_shape {

@@ -11,6 +11,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "common.cuh"
 #include "sbuild.cuh"
 
@@ -76,6 +78,9 @@ struct mbs_ctx {
     const float2** d_S32p = nullptr;
     RhsBody* d_rhsb = nullptr;
     std::map<std::pair<int64_t, int>, int*> split_cache;  // (targets, nsplit) -> split_body
+
+    // cuBLAS handle for the tall-skinny GEMMs of block GMRES (created lazily)
+    cublasHandle_t blas = nullptr;
 
     // live timing of the G_hat kernels (mbs_profile)
     bool profile = false;
@@ -544,6 +549,313 @@ GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol
     return S;
 }
 
+// ---------------------------------------------------------------------------
+// Block GMRES: the nrhs right-hand sides share one block Krylov space
+// span{R0, A R0, A^2 R0, ...} (each step applies the operator to an N x s
+// block, exactly like the lockstep GMRES, but every RHS minimises over all
+// s*j directions).  Block classical Gram-Schmidt applied twice with cuBLAS
+// GEMMs on the [s][N] blocks; the new block is orthonormalised by CholQR2
+// (Gram matrix and Cholesky on the host in FP64, triangular solve on the
+// device); the block upper Hessenberg least-squares problem is reduced by
+// Givens rotations on the host in FP64.
+// ---------------------------------------------------------------------------
+template <typename V>
+struct Blas;
+template <>
+struct Blas<float2> {
+    using C = cuComplex;
+    static C make(double re, double im) { return make_cuComplex((float)re, (float)im); }
+    static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
+                               int k, C alpha, const float2* A, int lda, const float2* B, int ldb, C beta,
+                               float2* Cm, int ldc) {
+        return cublasCgemm(h, ta, tb, m, n, k, &alpha, (const C*)A, lda, (const C*)B, ldb, &beta,
+                           (C*)Cm, ldc);
+    }
+    static cublasStatus_t trsm_ru(cublasHandle_t h, int m, int n, const float2* R, float2* B) {
+        const C one = make(1.0, 0.0);
+        return cublasCtrsm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, m, n, &one, (const C*)R, n, (C*)B, m);
+    }
+};
+template <>
+struct Blas<double2> {
+    using C = cuDoubleComplex;
+    static C make(double re, double im) { return make_cuDoubleComplex(re, im); }
+    static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
+                               int k, C alpha, const double2* A, int lda, const double2* B, int ldb, C beta,
+                               double2* Cm, int ldc) {
+        return cublasZgemm(h, ta, tb, m, n, k, &alpha, (const C*)A, lda, (const C*)B, ldb, &beta,
+                           (C*)Cm, ldc);
+    }
+    static cublasStatus_t trsm_ru(cublasHandle_t h, int m, int n, const double2* R, double2* B) {
+        const C one = make(1.0, 0.0);
+        return cublasZtrsm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, m, n, &one, (const C*)R, n, (C*)B, m);
+    }
+};
+
+#define MBS_BLAS_TRY(call)                                                                   \
+    do {                                                                                     \
+        cublasStatus_t s_ = (call);                                                          \
+        if (s_ != CUBLAS_STATUS_SUCCESS)                                                     \
+            throw MbsError{MBS_ERR_CUDA, std::string(#call) + ": cuBLAS status " + std::to_string((int)s_)}; \
+    } while (0)
+
+cublasHandle_t blas_handle(mbs_ctx* c) {
+    if (!c->blas) MBS_BLAS_TRY(cublasCreate(&c->blas));
+    MBS_BLAS_TRY(cublasSetStream(c->blas, c->st));
+    MBS_BLAS_TRY(cublasSetPointerMode(c->blas, CUBLAS_POINTER_MODE_HOST));
+    return c->blas;
+}
+
+template <typename V>
+void to_host_cd(const V* d, size_t n, std::vector<cd>& out, cudaStream_t st) {
+    std::vector<V> h(n);
+    MBS_CUDA_TRY(cudaMemcpyAsync(h.data(), d, n * sizeof(V), cudaMemcpyDeviceToHost, st));
+    MBS_CUDA_TRY(cudaStreamSynchronize(st));
+    out.resize(n);
+    for (size_t i = 0; i < n; ++i) out[i] = cd((double)h[i].x, (double)h[i].y);
+}
+template <typename V>
+void from_host_cd(const std::vector<cd>& in, V* d, cudaStream_t st, std::vector<V>& stage) {
+    stage.resize(in.size());
+    for (size_t i = 0; i < in.size(); ++i) {
+        stage[i].x = (decltype(stage[i].x))in[i].real();
+        stage[i].y = (decltype(stage[i].y))in[i].imag();
+    }
+    MBS_CUDA_TRY(cudaMemcpyAsync(d, stage.data(), in.size() * sizeof(V), cudaMemcpyHostToDevice, st));
+}
+
+// Cholesky of an s x s Hermitian matrix (column-major): G = R^H R, R upper.
+// Returns false if G is not numerically positive definite.
+bool chol_upper(const std::vector<cd>& G, int s, std::vector<cd>& R) {
+    R.assign((size_t)s * s, cd(0.0));
+    double gmax = 0.0;
+    for (int i = 0; i < s; ++i) gmax = std::max(gmax, G[(size_t)i * s + i].real());
+    for (int j = 0; j < s; ++j) {
+        for (int i = 0; i <= j; ++i) {
+            cd sum = G[(size_t)j * s + i];  // G(i, j)
+            for (int k = 0; k < i; ++k) sum -= std::conj(R[(size_t)i * s + k]) * R[(size_t)j * s + k];
+            if (i == j) {
+                if (!(sum.real() > 1e-13 * gmax)) return false;
+                R[(size_t)j * s + j] = std::sqrt(sum.real());
+            } else {
+                R[(size_t)j * s + i] = sum / R[(size_t)i * s + i].real();
+            }
+        }
+    }
+    return true;
+}
+
+// W (N x s, [s][N]) = Q R with Q orthonormal: two Cholesky-QR passes.
+// Returns false on (numerical) rank deficiency.
+template <typename V>
+bool cholqr2(mbs_ctx* c, cublasHandle_t h, V* W, int64_t N, int s, V* d_small, std::vector<cd>& R) {
+    std::vector<cd> G, R1, R2;
+    std::vector<V> stage;
+    using B = Blas<V>;
+    for (int pass = 0; pass < 2; ++pass) {
+        MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, s, s, (int)N, B::make(1, 0), W, (int)N, W,
+                             (int)N, B::make(0, 0), d_small, s));
+        to_host_cd(d_small, (size_t)s * s, G, c->st);
+        std::vector<cd>& Rp = pass == 0 ? R1 : R2;
+        if (!chol_upper(G, s, Rp)) return false;
+        from_host_cd(Rp, d_small, c->st, stage);
+        MBS_BLAS_TRY(B::trsm_ru(h, (int)N, s, d_small, W));
+        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    // R = R2 R1
+    R.assign((size_t)s * s, cd(0.0));
+    for (int j = 0; j < s; ++j)
+        for (int i = 0; i <= j; ++i) {
+            cd sum = 0.0;
+            for (int k = i; k <= j; ++k) sum += R2[(size_t)k * s + i] * R1[(size_t)j * s + k];
+            R[(size_t)j * s + i] = sum;
+        }
+    return true;
+}
+
+template <typename V>
+GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, int restart,
+                  int maxit, bool verify) {
+    using B = Blas<V>;
+    const int64_t N = c->N;
+    const size_t NV = (size_t)s * N;
+    GmresStats S;
+    S.relres.assign(s, 0.0);
+    cublasHandle_t h = blas_handle(c);
+    const std::string sfx = sizeof(V) == 8 ? "32" : "64";
+    V* basis = scratch<V>(c, "bg_basis" + sfx, (size_t)(restart + 1) * NV);
+    V* w = scratch<V>(c, "gm_w" + sfx, NV);
+    V* r = scratch<V>(c, "gm_r" + sfx, NV);
+    V* d_h = scratch<V>(c, "bg_h" + sfx, (size_t)(restart + 1) * s * s);
+    V* d_small = scratch<V>(c, "bg_small" + sfx, (size_t)s * s);
+    double* d_inv = scratch<double>(c, "gm_inv", s);
+    const std::vector<double> bn = norms<V>(c, b, s);
+    if (x_zero) {
+        MBS_CUDA_TRY(cudaMemsetAsync(x, 0, NV * sizeof(V), c->st));
+        MBS_CUDA_TRY(cudaMemcpyAsync(r, b, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        apply_op<V>(c, s, x, w);
+        S.matvecs++;
+        launch_sub<V>(b, w, r, (int64_t)NV, c->st);
+    }
+    const int M = restart * s;         // columns of the block Hessenberg
+    const int ldH = (restart + 1) * s;  // its rows
+    std::vector<cd> H, G, Hcol, Rk, cs_, sn_;
+    std::vector<V> stage;
+    double prev_worst = 1e300;
+    while (true) {
+        const std::vector<double> beta = norms<V>(c, r, s);
+        double worst = 0.0;
+        bool all = true, zero_col = false;
+        for (int q = 0; q < s; ++q) {
+            const double rel = bn[q] > 0 ? beta[q] / bn[q] : 0.0;
+            S.relres[q] = rel;
+            worst = std::max(worst, rel);
+            all = all && rel <= tol;
+            zero_col = zero_col || beta[q] == 0.0;
+        }
+        if (all) {
+            S.converged = true;
+            break;
+        }
+        if (S.iters >= maxit || worst > 0.9 * prev_worst || zero_col) break;
+        prev_worst = worst;
+        // V_0 beta0 = R0 with unit-norm columns first (D^{-1}), so beta0 = Rq D
+        std::vector<double> inv(s);
+        for (int q = 0; q < s; ++q) inv[q] = 1.0 / beta[q];
+        MBS_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), s * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        launch_scale<V>(r, d_inv, basis, N, s, c->st);
+        std::vector<cd> Rq;
+        if (!cholqr2<V>(c, h, basis, N, s, d_small, Rq)) break;  // R0 numerically rank deficient
+        H.assign((size_t)ldH * M, cd(0.0));
+        G.assign((size_t)ldH * s, cd(0.0));  // right-hand side of the small LS, column-major ldH
+        for (int q = 0; q < s; ++q)
+            for (int i = 0; i <= q; ++i) G[(size_t)q * ldH + i] = Rq[(size_t)q * s + i] * beta[q];
+        cs_.assign((size_t)M * s, cd(1.0));
+        sn_.assign((size_t)M * s, cd(0.0));
+        int jdone = 0;
+        bool breakdown = false;
+        for (int j = 0; j < restart && S.iters < maxit; ++j) {
+            V* vj = basis + (size_t)j * NV;
+            apply_op<V>(c, s, vj, w);
+            S.matvecs++;
+            const int K = (j + 1) * s;
+            // block CGS2: Hcol = V^H W; W -= V Hcol (twice)
+            Hcol.assign((size_t)K * s, cd(0.0));
+            for (int pass = 0; pass < 2; ++pass) {
+                MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, K, s, (int)N, B::make(1, 0), basis,
+                                     (int)N, w, (int)N, B::make(0, 0), d_h, K));
+                MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, s, K, B::make(-1, 0), basis,
+                                     (int)N, d_h, K, B::make(1, 0), w, (int)N));
+                std::vector<cd> hp;
+                to_host_cd(d_h, (size_t)K * s, hp, c->st);
+                for (size_t e = 0; e < hp.size(); ++e) Hcol[e] += hp[e];
+            }
+            V* vn = basis + (size_t)(j + 1) * NV;
+            MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
+            if (!cholqr2<V>(c, h, vn, N, s, d_small, Rk)) {
+                breakdown = true;  // the new block adds no direction: the solution is in the space
+                Rk.assign((size_t)s * s, cd(0.0));
+            }
+            S.iters++;
+            jdone = j + 1;
+            // block column j of H: rows 0..K-1 from Hcol, rows K..K+s-1 from Rk
+            for (int a = 0; a < s; ++a) {
+                const int col = j * s + a;
+                cd* hc = &H[(size_t)col * ldH];
+                for (int i = 0; i < K; ++i) hc[i] = Hcol[(size_t)a * K + i];
+                for (int i = 0; i <= a; ++i) hc[K + i] = Rk[(size_t)a * s + i];
+                // previous rotations (in generation order)
+                for (int pc = 0; pc < col; ++pc)
+                    for (int t = 0; t < s; ++t) {
+                        const int row = pc + s - t;  // rotation on rows (row-1, row)
+                        if (row > (j + 1) * s + s - 1) continue;
+                        const cd cc = cs_[(size_t)pc * s + t], ss = sn_[(size_t)pc * s + t];
+                        const cd u = hc[row - 1], v = hc[row];
+                        hc[row - 1] = std::conj(cc) * u + std::conj(ss) * v;
+                        hc[row] = -ss * u + cc * v;
+                    }
+                // new rotations: zero rows col+s .. col+1 (bottom up)
+                for (int t = 0; t < s; ++t) {
+                    const int row = col + s - t;
+                    const cd u = hc[row - 1], v = hc[row];
+                    const double den = std::sqrt(std::norm(u) + std::norm(v));
+                    const cd cc = den > 0 ? u / den : cd(1.0), ss = den > 0 ? v / den : cd(0.0);
+                    cs_[(size_t)col * s + t] = cc;
+                    sn_[(size_t)col * s + t] = ss;
+                    hc[row - 1] = den;
+                    hc[row] = 0.0;
+                    for (int q = 0; q < s; ++q) {
+                        cd* gq = &G[(size_t)q * ldH];
+                        const cd gu = gq[row - 1], gv = gq[row];
+                        gq[row - 1] = std::conj(cc) * gu + std::conj(ss) * gv;
+                        gq[row] = -ss * gu + cc * gv;
+                    }
+                }
+            }
+            // residual of RHS q: norm of G rows (j+1)s .. (j+2)s-1
+            bool conv = true;
+            for (int q = 0; q < s; ++q) {
+                double rr = 0.0;
+                for (int i = (j + 1) * s; i < (j + 2) * s; ++i) rr += std::norm(G[(size_t)q * ldH + i]);
+                S.relres[q] = bn[q] > 0 ? std::sqrt(rr) / bn[q] : 0.0;
+                conv = conv && S.relres[q] <= tol;
+            }
+            if (conv || breakdown) break;
+        }
+        // Y = R^{-1} G(0:jdone*s, :), X += V Y
+        const int Mj = jdone * s;
+        std::vector<cd> Y((size_t)Mj * s, cd(0.0));
+        for (int q = 0; q < s; ++q)
+            for (int i = Mj - 1; i >= 0; --i) {
+                cd sum = G[(size_t)q * ldH + i];
+                for (int l = i + 1; l < Mj; ++l) sum -= H[(size_t)l * ldH + i] * Y[(size_t)q * Mj + l];
+                const cd dgl = H[(size_t)i * ldH + i];
+                Y[(size_t)q * Mj + i] = std::abs(dgl) > 0 ? sum / dgl : cd(0.0);
+            }
+        if (Mj > 0) {
+            V* d_y = scratch<V>(c, "bg_y" + sfx, (size_t)M * s);
+            from_host_cd(Y, d_y, c->st, stage);
+            MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, s, Mj, B::make(1, 0), basis,
+                                 (int)N, d_y, Mj, B::make(1, 0), x, (int)N));
+        }
+        bool est_conv = true;
+        for (int q = 0; q < s; ++q) est_conv = est_conv && S.relres[q] <= tol;
+        if (est_conv && !verify) {
+            S.converged = true;
+            break;
+        }
+        if (S.iters >= maxit && !verify) break;
+        apply_op<V>(c, s, x, w);
+        S.matvecs++;
+        launch_sub<V>(b, w, r, (int64_t)NV, c->st);
+        if (S.iters >= maxit) {
+            const std::vector<double> bt = norms<V>(c, r, s);
+            bool ok = true;
+            for (int q = 0; q < s; ++q) {
+                S.relres[q] = bn[q] > 0 ? bt[q] / bn[q] : 0.0;
+                ok = ok && S.relres[q] <= tol;
+            }
+            S.converged = ok;
+            break;
+        }
+    }
+    MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+    return S;
+}
+
+// Krylov solver choice: block GMRES for several right-hand sides (unless
+// disabled), lockstep GMRES otherwise.
+template <typename V>
+GmresStats krylov(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol, int restart,
+                  int maxit, bool verify) {
+    if (nrhs > 1 && c->opt.block_krylov)
+        return bgmres<V>(c, nrhs, b, x, x_zero, tol, restart, maxit, verify);
+    return gmres<V>(c, nrhs, b, x, x_zero, tol, restart, maxit, verify);
+}
+
 void validate_options(const mbs_options& o) {
     if (o.precision != MBS_PREC_FP64 && o.precision != MBS_PREC_MIXED && o.precision != MBS_PREC_FP32)
         throw MbsError{MBS_ERR_ARG, "precision must be MBS_PREC_FP64, MBS_PREC_MIXED or MBS_PREC_FP32"};
@@ -914,6 +1226,7 @@ void mbs_default_options(mbs_options* o) {
     o->stream = nullptr;
     o->hbm_budget = 0;
     o->tile_override = 0;
+    o->block_krylov = 1;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {
@@ -999,6 +1312,7 @@ void mbs_destroy(mbs_ctx* c) {
         for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
         for (auto& kv : c->bufs) dfree(c, kv.second.p);
         c->bufs.clear();
+        if (c->blas) cublasDestroy(c->blas);
         if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     }
     delete c;
@@ -1133,7 +1447,7 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
         double relmax = 0.0;
         const mbs_options& o = c->opt;
         if (o.precision == MBS_PREC_FP64 || o.precision == MBS_PREC_FP32) {
-            GmresStats S = gmres<double2>(c, nrhs, db, ox.dev, xzero, o.tol, o.restart, o.max_iter, true);
+            GmresStats S = krylov<double2>(c, nrhs, db, ox.dev, xzero, o.tol, o.restart, o.max_iter, true);
             inf.inner_iterations = S.iters;
             inf.matvecs_fp64 = S.matvecs;
             inf.sweeps = 1;
@@ -1178,7 +1492,7 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
                 }
                 MBS_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
                 launch_f64_to_f32_scaled(r64, d_sc, r32, c->N, nrhs, c->st);
-                GmresStats S = gmres<float2>(c, nrhs, r32, d32, true, o.inner_tol, o.restart,
+                GmresStats S = krylov<float2>(c, nrhs, r32, d32, true, o.inner_tol, o.restart,
                                              o.max_iter - inf.inner_iterations, false);
                 inf.inner_iterations += S.iters;
                 inf.matvecs_fp32 += S.matvecs;
