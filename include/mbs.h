@@ -76,6 +76,7 @@ typedef struct mbs_options {
     size_t hbm_budget;   /* bytes of device memory the context may hold (0 = no cap) */
     int tile_override;   /* 0 = tuned launch shape; >0 forces the source-split count of G_hat */
     int block_krylov;    /* 1 (default): several right-hand sides share one block Krylov space; 0: independent GMRES in lockstep */
+    int mac_path;        /* FP32 G_hat multiply-add: 0 auto (the faster, currently the FP32 pipe), 1 FP32 pipe, 2 tensor cores (3xTF32 mma.sync) */
 } mbs_options;
 
 typedef struct mbs_shape {

@@ -296,7 +296,7 @@ void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
         e1 = take_event(c);
         c->ev32.emplace_back(e0, e1);
     }
-    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st, e0, e1);
+    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st, e0, e1, c->opt.mac_path);
 }
 void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
     int ns;
@@ -1227,6 +1227,7 @@ void mbs_default_options(mbs_options* o) {
     o->hbm_budget = 0;
     o->tile_override = 0;
     o->block_krylov = 1;
+    o->mac_path = 0;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {

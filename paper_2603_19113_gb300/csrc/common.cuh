@@ -85,9 +85,10 @@ void launch_pair_table(int dim, int T, const double* d_centres, const double* d_
                        double kappa, float4* pair, float* pair_phi0, cudaStream_t st);
 // ev0/ev1 (nullable) are recorded on st around the G_hat kernel launches
 // (not the split reduction), for live timing of the dominant kernel.
+// mac_path: 0 auto (FP32 pipe, measured faster), 1 FP32 pipe, 2 tensor cores.
 void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
                   float2* part, int nsplit, const int* d_split_body, cudaStream_t st,
-                  cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                  cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int mac_path = 0);
 void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);

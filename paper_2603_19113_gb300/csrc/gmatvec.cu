@@ -61,7 +61,9 @@ struct F32Const {
 // exp(i ph) reduced to [-pi, pi] by a two-constant Cody-Waite step (6.28125 is
 // exact in 8 bits, so n * 6.28125 is exact for the |n| < 2^16 that occur).
 __device__ __forceinline__ float2 expi_f32(float ph) {
-    const float n = rintf(ph * 0.159154943091895336f);
+    // n = nearest integer to ph / (2 pi), by adding and removing 1.5 * 2^23
+    // (exact for |ph / 2 pi| < 2^22; keeps the rounding off the XU pipe)
+    const float n = fmaf(ph, 0.159154943091895336f, 12582912.f) - 12582912.f;
     ph = fmaf(-n, 6.28125f, ph);
     ph = fmaf(-n, 1.93530717958647692e-3f, ph);
     float sn, cs;
@@ -235,6 +237,186 @@ __global__ void __launch_bounds__(TPB) g_f32_kernel(const GLayout L, const F32Co
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 G_hat with the multiply-add on the tensor cores.
+//
+// phi is computed on the FP32 pipe exactly as above; the product of a tile of
+// phi (8 targets x 4 sources) with the staged right-hand sides (4 sources x 8
+// RHS) is one mma.m16n8k8 in the real embedding
+//     [Yr; Yi] = [Phi_r  -Phi_i; Phi_i  Phi_r] [Qr; Qi]
+// (rows 0-7: real parts of the 8 targets, rows 8-15: imaginary parts; k 0-3:
+// real parts of the 4 sources' q, k 4-7: imaginary parts).  In the m16n8k8
+// fragment layout, lane (g = lane/4, t = lane%4) holds A[g][t], A[g+8][t],
+// A[g][t+4], A[g+8][t+4] = Phi_r, Phi_i, -Phi_i, Phi_r of ONE pair (target g,
+// source t), so every lane evaluates exactly one phi per MMA.  FP32 accuracy
+// comes from the 3xTF32 split x = hi + lo (hi = round-to-TF32(x)):
+// phi q ~ hi(phi) hi(q) + hi(phi) lo(q) + lo(phi) hi(q), accumulated in FP32.
+// ---------------------------------------------------------------------------
+// High part of the split: x with its 13 low mantissa bits cleared (a TF32
+// value; one logic op instead of a conversion on the XU pipe).  The low part
+// x - hi is exact in FP32; the MMA reads its top 10 mantissa bits, so a
+// product keeps ~2^-20 relative accuracy.
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    return __float_as_uint(x) & 0xffffe000u;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int TC_WARPS = 4;
+constexpr int TC_TW = 4;  // 8-target tiles per warp
+constexpr int TC_TARGETS = TC_WARPS * TC_TW * 8;
+
+template <int DIM, int NRB>
+__global__ void __launch_bounds__(TC_WARPS * 32) g_tc_kernel(const GLayout L, const F32Const K,
+                                                             const int nrhs, const int r0,
+                                                             const float2* __restrict__ q,
+                                                             float2* __restrict__ part,
+                                                             const int* __restrict__ split_body) {
+    // staged sources: local offsets and the TF32 split of q, [part][rb][source][rhs]
+    // with part = {hi re, hi im, lo re, lo im}
+    __shared__ float s_loc[DIM][SB];
+    __shared__ uint32_t s_q[4][NRB][SB][8];
+    const int64_t N = L.N;
+    const int T = L.T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t tile0 = (int64_t)blockIdx.x * TC_TARGETS + warp * (TC_TW * 8);
+    bool valid[TC_TW];
+    int tb[TC_TW];
+    float d[TC_TW][DIM];
+    float acc[TC_TW][NRB][4];
+#pragma unroll
+    for (int k = 0; k < TC_TW; ++k) {
+        const int64_t i = tile0 + 8 * k + g;
+        valid[k] = i < N;
+        tb[k] = valid[k] ? L.body[i] : -1;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) d[k][c] = valid[k] ? L.loc32[c * N + i] : 0.f;
+#pragma unroll
+        for (int rb = 0; rb < NRB; ++rb)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[k][rb][e] = 0.f;
+    }
+    const int sb0 = split_body[blockIdx.y], sb1 = split_body[blockIdx.y + 1];
+    for (int sb = sb0; sb < sb1; ++sb) {
+        const int64_t js = L.off[sb], je = L.off[sb + 1];
+        bool act[TC_TW];
+        float4 P[TC_TW];
+        float R2[TC_TW], f0[TC_TW];
+        bool fast_lane = true;
+#pragma unroll
+        for (int k = 0; k < TC_TW; ++k) {
+            act[k] = valid[k] && tb[k] != sb;  // zero diagonal blocks of G_hat
+            P[k] = act[k] ? L.pair[(int64_t)tb[k] * T + sb] : make_float4(0.f, 0.f, 1.f, 1.f);
+            f0[k] = (DIM == 3 && act[k]) ? L.pair_phi0[(int64_t)tb[k] * T + sb] : 0.f;
+            if (DIM == 2) {  // a negative R marks a near body pair
+                fast_lane = fast_lane && act[k] && P[k].z > 0.f;
+                P[k].z = fabsf(P[k].z);
+            } else {
+                fast_lane = fast_lane && act[k];
+            }
+            const float R = DIM == 2 ? P[k].z : P[k].w;
+            R2[k] = R * R;
+        }
+        const bool fast = __all_sync(0xffffffffu, fast_lane);
+        for (int64_t jc = js; jc < je; jc += SB) {
+            const int n = (int)min((int64_t)SB, je - jc);
+            const int n4 = (n + 3) & ~3;
+            __syncthreads();
+            for (int j = tid; j < n4; j += blockDim.x) {
+                const bool sv = j < n;
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) s_loc[c][j] = sv ? L.loc32[c * N + jc + j] : 0.f;
+#pragma unroll
+                for (int rb = 0; rb < NRB; ++rb)
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const int rr = r0 + rb * 8 + r;
+                        const float2 v = (sv && rr < nrhs) ? q[(int64_t)rr * N + jc + j]
+                                                           : make_float2(0.f, 0.f);
+                        const uint32_t hr = f32_to_tf32(v.x), hi = f32_to_tf32(v.y);
+                        s_q[0][rb][j][r] = hr;
+                        s_q[1][rb][j][r] = hi;
+                        s_q[2][rb][j][r] = __float_as_uint(v.x - __uint_as_float(hr));
+                        s_q[3][rb][j][r] = __float_as_uint(v.y - __uint_as_float(hi));
+                    }
+            }
+            __syncthreads();
+            // the tensor cores accumulate one staged chunk (<= 128 sources) into a
+            // fresh tile; the chunk sums are added on the FP32 pipe, so rounding in
+            // the MMA accumulator does not grow with the number of sources
+            float tacc[TC_TW][NRB][4];
+#pragma unroll
+            for (int k = 0; k < TC_TW; ++k)
+#pragma unroll
+                for (int rb = 0; rb < NRB; ++rb)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) tacc[k][rb][e] = 0.f;
+            for (int c4 = 0; c4 < n4; c4 += 4) {
+                const int j = c4 + t;
+                const bool sv = j < n;
+                float dj[DIM];
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) dj[c] = s_loc[c][j];
+                uint32_t bh0[NRB], bh1[NRB], bl0[NRB], bl1[NRB];
+#pragma unroll
+                for (int rb = 0; rb < NRB; ++rb) {
+                    bh0[rb] = s_q[0][rb][j][g];
+                    bh1[rb] = s_q[1][rb][j][g];
+                    bl0[rb] = s_q[2][rb][j][g];
+                    bl1[rb] = s_q[3][rb][j][g];
+                }
+#pragma unroll
+                for (int k = 0; k < TC_TW; ++k) {
+                    float2 ph;
+                    if (fast)
+                        ph = pair_phi_f32<DIM, true>(d[k], dj, P[k], R2[k], f0[k], K);
+                    else
+                        ph = (act[k] && sv) ? pair_phi_f32<DIM, false>(d[k], dj, P[k], R2[k], f0[k], K)
+                                            : make_float2(0.f, 0.f);
+                    __syncwarp();
+                    const uint32_t hr = f32_to_tf32(ph.x), hi = f32_to_tf32(ph.y);
+                    const uint32_t lr = __float_as_uint(ph.x - __uint_as_float(hr));
+                    const uint32_t li = __float_as_uint(ph.y - __uint_as_float(hi));
+                    const uint32_t ah[4] = {hr, hi, hi ^ 0x80000000u, hr};
+                    const uint32_t al[4] = {lr, li, li ^ 0x80000000u, lr};
+#pragma unroll
+                    for (int rb = 0; rb < NRB; ++rb) {
+                        mma_tf32(tacc[k][rb], ah, bh0[rb], bh1[rb]);
+                        mma_tf32(tacc[k][rb], ah, bl0[rb], bl1[rb]);
+                        mma_tf32(tacc[k][rb], al, bh0[rb], bh1[rb]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < TC_TW; ++k)
+#pragma unroll
+                for (int rb = 0; rb < NRB; ++rb)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[k][rb][e] += tacc[k][rb][e];
+        }
+    }
+    // acc[k][rb] = {Yr(g, 2t), Yr(g, 2t+1), Yi(g, 2t), Yi(g, 2t+1)}
+    float2* out = part + (int64_t)blockIdx.y * nrhs * N;
+#pragma unroll
+    for (int k = 0; k < TC_TW; ++k) {
+        if (!valid[k]) continue;
+        const int64_t i = tile0 + 8 * k + g;
+#pragma unroll
+        for (int rb = 0; rb < NRB; ++rb) {
+            const int rr = r0 + rb * 8 + 2 * t;
+            if (rr < nrhs) out[(int64_t)rr * N + i] = make_float2(acc[k][rb][0], acc[k][rb][2]);
+            if (rr + 1 < nrhs) out[(int64_t)(rr + 1) * N + i] = make_float2(acc[k][rb][1], acc[k][rb][3]);
+        }
+    }
+}
+
 // FP64 path: world coordinates, no phase split.  Used for the FP64 operator,
 // the refinement residual and field evaluation (tbody == nullptr: no mask).
 template <int DIM, int NR>
@@ -347,12 +529,20 @@ void launch_f32_chunk(const GLayout& L, const F32Const& K, int nrhs, int r0,
 }
 
 template <int DIM>
-void launch_f32_dim(const GLayout& L, const F32Const& K, int nrhs,
+void launch_f32_dim(const GLayout& L, const F32Const& K, int nrhs, bool tensor,
                     const float2* q, float2* part, int nsplit, const int* sb, cudaStream_t st) {
     int r0 = 0;
     while (r0 < nrhs) {
         const int left = nrhs - r0;
-        if (left >= 16) {
+        if (tensor && left > 8) {
+            dim3 grid((unsigned)((L.N + TC_TARGETS - 1) / TC_TARGETS), (unsigned)nsplit);
+            g_tc_kernel<DIM, 2><<<grid, TC_WARPS * 32, 0, st>>>(L, K, nrhs, r0, q, part, sb);
+            r0 += 16;
+        } else if (tensor) {
+            dim3 grid((unsigned)((L.N + TC_TARGETS - 1) / TC_TARGETS), (unsigned)nsplit);
+            g_tc_kernel<DIM, 1><<<grid, TC_WARPS * 32, 0, st>>>(L, K, nrhs, r0, q, part, sb);
+            r0 += 8;
+        } else if (left >= 16) {
             launch_f32_chunk<DIM, 16>(L, K, nrhs, r0, q, part, nsplit, sb, st);
             r0 += 16;
         } else if (left > 4) {
@@ -422,18 +612,23 @@ void launch_pair_table(int dim, int T, const double* d_centres, const double* d_
 
 void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
                   float2* part, int nsplit, const int* d_split_body, cudaStream_t st,
-                  cudaEvent_t ev0, cudaEvent_t ev1) {
+                  cudaEvent_t ev0, cudaEvent_t ev1, int mac_path) {
     if (L.N == 0 || nrhs == 0) return;
     F32Const K;
     K.kappa = (float)kappa;
     K.ampc = (float)(0.25 * sqrt(2.0 / (MBS_PI * kappa)));
     K.c8 = (float)(2.0 * MBS_F32_X8_XA / kappa);
     K.c3 = (float)(2.0 * MBS_F32_X3_XA / kappa);
+    // Measured on GB300 (1000-body workload, 8 RHS): FP32-pipe multiply-add
+    // 9.6 ms per launch, tensor-core (mma.sync 3xTF32) 10.8 ms: the split and
+    // the three MMAs per tile do not hide behind the phi evaluation, so the
+    // automatic choice is the FP32 pipe; mac_path = 2 selects the tensor cores.
+    const bool tensor = mac_path == 2;
     if (ev0) MBS_CUDA_TRY(cudaEventRecord(ev0, st));
     if (L.dim == 2)
-        launch_f32_dim<2>(L, K, nrhs, q, part, nsplit, d_split_body, st);
+        launch_f32_dim<2>(L, K, nrhs, tensor, q, part, nsplit, d_split_body, st);
     else
-        launch_f32_dim<3>(L, K, nrhs, q, part, nsplit, d_split_body, st);
+        launch_f32_dim<3>(L, K, nrhs, tensor, q, part, nsplit, d_split_body, st);
     if (ev1) MBS_CUDA_TRY(cudaEventRecord(ev1, st));
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<float2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
