@@ -54,10 +54,49 @@ def parse():
                     help="steps of the end-to-end (host buffers) measurement")
     ap.add_argument("--fp64-iters", type=int, default=12,
                     help="iterations of the capped FP64 solve used for its time estimate")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the served trace (0 = skip); body counts scaled to 20..300")
+    ap.add_argument("--serve-tmax", type=int, default=300)
     ap.add_argument("--kernel", choices=["g32", "g64"], default=None,
                     help="only apply G_hat (FP32 or FP64) to 8 random vectors, steps times "
                          "(for profiling the dominant kernel); prints per-launch times")
     return ap.parse_args()
+
+
+def run_serving(a, pkg, mi):
+    """Replay a prefix of the serving trace (exponential arrivals at 20/s,
+    2D/3D mix 70/30, kappa ~ U(5, 50), 1..32 right-hand sides) against the
+    continuous-batching server; latency = completion - arrival."""
+    import numpy as np
+    trace = mi.serving_trace(seed=0, n=a.serve_requests, Tmin=20, Tmax=a.serve_tmax)
+    work = [(r, mi.request_workload(r)) for r in trace]
+    data = [(r, wl, wl.boundary_data()) for r, wl in work]
+    srv = pkg.Server(max_active=4)
+    t0 = time.perf_counter()
+    ids = []
+    for r, wl, v in data:
+        delay = r.arrival - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append((r, srv.submit(wl, v, tol=1e-9)))
+    srv.drain()
+    lat, done, fails = [], [], 0
+    for r, rid in ids:
+        res = srv.poll(rid)
+        if res["done"] != 1:
+            fails += 1
+            continue
+        lat.append(res["t_end"] - res["t_submit"])
+        done.append(res["t_end"])
+    first = min(srv.poll(rid)["t_submit"] for _, rid in ids)
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(ids), "failed": fails,
+            "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "solves_per_s": len(done) / (max(done) - first) if done else None,
+            "trace": f"first {len(ids)} requests of the seed-0 trace, body counts 20..{a.serve_tmax}, "
+                     "mixed precision to rel. residual 1e-9, 4 concurrent slots"}
 
 
 def run_kernel_only(a):
@@ -417,6 +456,10 @@ def run_mbs(a, ws, rank, local):
                 "peak_note": "FP32 SIMT peak from unit counts: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     share = kt["g32_ms"] / ms if ms > 0 else None
 
+    served = None
+    if rank == 0 and a.serve_requests > 0:
+        served = run_serving(a, pkg, mi)
+
     cpu = None
     if pool is not None:
         import oracle  # noqa: F401  (test infrastructure: CPU baseline leg only)
@@ -445,6 +488,7 @@ def run_mbs(a, ws, rank, local):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

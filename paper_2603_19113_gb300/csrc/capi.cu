@@ -846,12 +846,14 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
     return S;
 }
 
-// Krylov solver choice: block GMRES for several right-hand sides (unless
-// disabled), lockstep GMRES otherwise.
+// Krylov solver choice: block GMRES for 2..16 right-hand sides (unless
+// disabled), lockstep GMRES otherwise.  The host-side Givens reduction of the
+// block Hessenberg matrix costs O(j s^3) per step, which grows too fast beyond
+// 16 right-hand sides.
 template <typename V>
 GmresStats krylov(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol, int restart,
                   int maxit, bool verify) {
-    if (nrhs > 1 && c->opt.block_krylov)
+    if (nrhs > 1 && nrhs <= 16 && c->opt.block_krylov)
         return bgmres<V>(c, nrhs, b, x, x_zero, tol, restart, maxit, verify);
     return gmres<V>(c, nrhs, b, x, x_zero, tol, restart, maxit, verify);
 }
