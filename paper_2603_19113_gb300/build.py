@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-lpthread",
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread",
            "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:

@@ -93,18 +93,17 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 // partial[(i*nrhs + r) * nblk + blk] = sum over the block's slice of conj(basis_{i,r}) . w_r
 // for every i < nvec.  The block keeps its slice of w_r in registers and walks
 // the basis vectors; per-thread sums are in the vector's precision, the
-// cross-warp sums in FP64.
+// cross-warp sums in FP64 and in a fixed order (bitwise reproducible).
 template <typename V>
 __global__ void __launch_bounds__(256) dots_kernel(const V* __restrict__ basis, const int nvec,
                                                    const V* __restrict__ w, const int64_t N,
                                                    const int nrhs, double2* __restrict__ partial,
                                                    const int nblk) {
     using T = typename Acc<V>::T;
-    extern __shared__ double2 s_acc[];
+    extern __shared__ double2 s_acc[];  // [warp][nvec]
     const int r = blockIdx.y, blk = blockIdx.x;
     const int64_t chunk = (N + nblk - 1) / nblk;
     const int64_t n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s_acc[i] = make_double2(0.0, 0.0);
     V wv[DOT_E];
 #pragma unroll
     for (int e = 0; e < DOT_E; ++e) {
@@ -113,7 +112,7 @@ __global__ void __launch_bounds__(256) dots_kernel(const V* __restrict__ basis, 
         z.x = z.y = T(0);
         wv[e] = n < n1 ? w[(int64_t)r * N + n] : z;
     }
-    __syncthreads();
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int i = 0; i < nvec; ++i) {
         const V* __restrict__ vb = basis + ((int64_t)i * nrhs + r) * N;
         T sx = T(0), sy = T(0);
@@ -128,14 +127,15 @@ __global__ void __launch_bounds__(256) dots_kernel(const V* __restrict__ basis, 
         }
         sx = warp_sum_t(sx);
         sy = warp_sum_t(sy);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&s_acc[i].x, (double)sx);
-            atomicAdd(&s_acc[i].y, (double)sy);
-        }
+        if ((threadIdx.x & 31) == 0) s_acc[(int64_t)warp * nvec + i] = make_double2(sx, sy);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x)
-        partial[((int64_t)i * nrhs + r) * nblk + blk] = s_acc[i];
+    // warps are summed in a fixed order: the result does not depend on scheduling
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        double2 s = s_acc[i];
+        for (int wi = 1; wi < nwarp; ++wi) s = cadd(s, s_acc[(int64_t)wi * nvec + i]);
+        partial[((int64_t)i * nrhs + r) * nblk + blk] = s;
+    }
 }
 
 __global__ void dots_finish_kernel(const double2* __restrict__ partial, int count, int nblk,
@@ -269,6 +269,182 @@ __global__ void f64_to_f32_kernel(const double2* __restrict__ a, float2* __restr
 
 inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// ---------------------------------------------------------------------------
+// Tall-skinny products of block GMRES.  A block of k vectors of length N is
+// stored [k][N].  Every reduction runs in a fixed order, so a solve returns
+// bitwise the same result whatever else runs on the device at the same time.
+//   ts_gram:   C (ka x kb, column-major) = A^H B            (FP64 result)
+//   ts_update: B += alpha A H, H ka x kb column-major (FP64)
+//   ts_trsm:   B <- B R^{-1}, R kb x kb upper triangular (FP64)
+// ---------------------------------------------------------------------------
+constexpr int TSG_A = 4, TSG_B = 8;  // output tile of one ts_gram block
+
+// partial[(b * ka + a) * nblk + blk] = sum over the block's rows of conj(A_a) B_b
+template <typename V>
+__global__ void __launch_bounds__(256) ts_gram_kernel(const V* __restrict__ A, const int ka,
+                                                      const V* __restrict__ B, const int kb,
+                                                      const int64_t N, double2* __restrict__ partial,
+                                                      const int nblk) {
+    using T = typename Acc<V>::T;
+    __shared__ double2 s_w[8][TSG_A * TSG_B];
+    const int blk = blockIdx.x, a0 = blockIdx.y * TSG_A, b0 = blockIdx.z * TSG_B;
+    const int64_t chunk = (N + nblk - 1) / nblk;
+    const int64_t n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+    T ax[TSG_A][TSG_B], ay[TSG_A][TSG_B];
+#pragma unroll
+    for (int a = 0; a < TSG_A; ++a)
+#pragma unroll
+        for (int b = 0; b < TSG_B; ++b) ax[a][b] = ay[a][b] = T(0);
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+        V bv[TSG_B];
+#pragma unroll
+        for (int b = 0; b < TSG_B; ++b) {
+            if (b0 + b < kb) {
+                bv[b] = B[(int64_t)(b0 + b) * N + n];
+            } else {
+                bv[b].x = T(0);
+                bv[b].y = T(0);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < TSG_A; ++a) {
+            if (a0 + a < ka) {
+                const V av = A[(int64_t)(a0 + a) * N + n];
+#pragma unroll
+                for (int b = 0; b < TSG_B; ++b) {
+                    ax[a][b] = fma(av.x, bv[b].x, fma(av.y, bv[b].y, ax[a][b]));
+                    ay[a][b] = fma(av.x, bv[b].y, fma(-av.y, bv[b].x, ay[a][b]));
+                }
+            }
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < TSG_A; ++a)
+#pragma unroll
+        for (int b = 0; b < TSG_B; ++b) {
+            const T sx = warp_sum_t(ax[a][b]);
+            const T sy = warp_sum_t(ay[a][b]);
+            if (lane == 0) s_w[warp][a * TSG_B + b] = make_double2((double)sx, (double)sy);
+        }
+    __syncthreads();
+    if (threadIdx.x < TSG_A * TSG_B) {
+        const int a = threadIdx.x / TSG_B, b = threadIdx.x % TSG_B;
+        if (a0 + a < ka && b0 + b < kb) {
+            double2 s = s_w[0][threadIdx.x];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, s_w[w][threadIdx.x]);
+            partial[((int64_t)(b0 + b) * ka + (a0 + a)) * nblk + blk] = s;
+        }
+    }
+}
+
+constexpr int TSU_CH = 128;  // coefficient rows staged per round
+
+// B_b += alpha sum_a A_a H(a, b) for b < kb <= KB; one row per thread.
+template <typename V, int KB>
+__global__ void __launch_bounds__(256) ts_update_kernel(const V* __restrict__ A, const int ka,
+                                                        const double2* __restrict__ H,
+                                                        const double alpha, V* __restrict__ B,
+                                                        const int kb, const int64_t N) {
+    using T = typename Acc<V>::T;
+    __shared__ V s_h[TSU_CH][KB];
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    T bx[KB], by[KB];
+#pragma unroll
+    for (int b = 0; b < KB; ++b) bx[b] = by[b] = T(0);
+    for (int c0 = 0; c0 < ka; c0 += TSU_CH) {
+        const int nc = min(TSU_CH, ka - c0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nc * KB; idx += blockDim.x) {
+            const int a = idx / KB, b = idx - a * KB;
+            V hv;
+            if (b < kb) {
+                const double2 h = H[(int64_t)b * ka + c0 + a];
+                hv.x = (T)(alpha * h.x);
+                hv.y = (T)(alpha * h.y);
+            } else {
+                hv.x = T(0);
+                hv.y = T(0);
+            }
+            s_h[a][b] = hv;
+        }
+        __syncthreads();
+        if (n < N) {
+            for (int a = 0; a < nc; ++a) {
+                const V av = A[(int64_t)(c0 + a) * N + n];
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+                    const V h = s_h[a][b];
+                    bx[b] = fma(av.x, h.x, fma(-av.y, h.y, bx[b]));
+                    by[b] = fma(av.x, h.y, fma(av.y, h.x, by[b]));
+                }
+            }
+        }
+    }
+    if (n < N) {
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            if (b < kb) {
+                V o = B[(int64_t)b * N + n];
+                o.x += bx[b];
+                o.y += by[b];
+                B[(int64_t)b * N + n] = o;
+            }
+        }
+    }
+}
+
+// B <- B R^{-1} (forward substitution along each row); R upper, kb <= KB.
+template <typename V, int KB>
+__global__ void __launch_bounds__(256) ts_trsm_kernel(V* __restrict__ B, const int kb,
+                                                      const int64_t N,
+                                                      const double2* __restrict__ R) {
+    using T = typename Acc<V>::T;
+    __shared__ V s_r[KB][KB];  // s_r[i][j] = R(i, j), i <= j
+    __shared__ V s_inv[KB];    // 1 / R(j, j)
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        const int i = idx % kb, j = idx / kb;
+        const double2 r = R[(int64_t)j * kb + i];
+        V rv;
+        rv.x = (T)r.x;
+        rv.y = (T)r.y;
+        s_r[i][j] = rv;
+        if (i == j) {
+            const double d = cabs2(r);
+            V iv;
+            iv.x = (T)(r.x / d);
+            iv.y = (T)(-r.y / d);
+            s_inv[j] = iv;
+        }
+    }
+    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    T xr[KB], xi[KB];
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+        if (j < kb) {
+            const V v = B[(int64_t)j * N + n];
+            T sr = v.x, si = v.y;
+#pragma unroll
+            for (int k = 0; k < j; ++k) {
+                const V r = s_r[k][j];
+                sr = fma(-xr[k], r.x, fma(xi[k], r.y, sr));
+                si = fma(-xr[k], r.y, fma(-xi[k], r.x, si));
+            }
+            const V iv = s_inv[j];
+            xr[j] = sr * iv.x - si * iv.y;
+            xi[j] = sr * iv.y + si * iv.x;
+            V o;
+            o.x = xr[j];
+            o.y = xi[j];
+            B[(int64_t)j * N + n] = o;
+        } else {
+            xr[j] = xi[j] = T(0);
+        }
+    }
+}
+
 }  // namespace
 
 int mbs_num_sms() {
@@ -311,7 +487,8 @@ void launch_dots(const V* basis, int nvec, const V* w, int64_t N, int nrhs, doub
     if ((int64_t)nblk * 256 * DOT_E < N)
         throw MbsError{MBS_ERR_ARG, "launch_dots: too few blocks for the vector length"};
     dim3 g((unsigned)nblk, (unsigned)nrhs);
-    const size_t sm = (size_t)nvec * sizeof(double2);
+    const size_t sm = (size_t)nvec * (256 / 32) * sizeof(double2);
+    if (sm > 227 * 1024) throw MbsError{MBS_ERR_ARG, "launch_dots: too many basis vectors"};
     if (sm > 48 * 1024)
         MBS_CUDA_TRY(cudaFuncSetAttribute(dots_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm));
@@ -399,3 +576,61 @@ void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st) 
     f64_to_f32_kernel<<<nblocks(n), 256, 0, st>>>(a, b, n);
     MBS_CHECK_LAUNCH();
 }
+
+// ---------------------------------------------------------------------------
+// tall-skinny block products (block GMRES)
+// ---------------------------------------------------------------------------
+int ts_gram_blocks(int64_t N, int ka, int kb) {
+    const int64_t tiles = (int64_t)((ka + TSG_A - 1) / TSG_A) * ((kb + TSG_B - 1) / TSG_B);
+    const int64_t want = (8LL * mbs_num_sms() + tiles - 1) / tiles;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((N + 2047) / 2048, want));
+}
+
+template <typename V>
+void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* C,
+                    double2* scratch, int nblk, cudaStream_t st) {
+    if (ka == 0 || kb == 0) return;
+    if (N == 0) {
+        MBS_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)ka * kb * sizeof(double2), st));
+        return;
+    }
+    dim3 g((unsigned)nblk, (unsigned)((ka + TSG_A - 1) / TSG_A), (unsigned)((kb + TSG_B - 1) / TSG_B));
+    ts_gram_kernel<V><<<g, 256, 0, st>>>(A, ka, B, kb, N, scratch, nblk);
+    MBS_CHECK_LAUNCH();
+    dots_finish_kernel<<<nblocks((int64_t)ka * kb, 128), 128, 0, st>>>(scratch, ka * kb, nblk, C);
+    MBS_CHECK_LAUNCH();
+}
+
+template <typename V>
+void launch_ts_update(const V* A, int ka, const double2* H, double alpha, V* B, int kb, int64_t N,
+                      cudaStream_t st) {
+    if (ka == 0 || kb == 0 || N == 0) return;
+    if (kb > 16) throw MbsError{MBS_ERR_ARG, "launch_ts_update: more than 16 columns"};
+    if (kb <= 8)
+        ts_update_kernel<V, 8><<<nblocks(N), 256, 0, st>>>(A, ka, H, alpha, B, kb, N);
+    else
+        ts_update_kernel<V, 16><<<nblocks(N), 256, 0, st>>>(A, ka, H, alpha, B, kb, N);
+    MBS_CHECK_LAUNCH();
+}
+
+template <typename V>
+void launch_ts_trsm(V* B, int kb, int64_t N, const double2* R, cudaStream_t st) {
+    if (kb == 0 || N == 0) return;
+    if (kb > 16) throw MbsError{MBS_ERR_ARG, "launch_ts_trsm: more than 16 columns"};
+    if (kb <= 8)
+        ts_trsm_kernel<V, 8><<<nblocks(N), 256, 0, st>>>(B, kb, N, R);
+    else
+        ts_trsm_kernel<V, 16><<<nblocks(N), 256, 0, st>>>(B, kb, N, R);
+    MBS_CHECK_LAUNCH();
+}
+
+template void launch_ts_gram<float2>(const float2*, int, const float2*, int, int64_t, double2*,
+                                     double2*, int, cudaStream_t);
+template void launch_ts_gram<double2>(const double2*, int, const double2*, int, int64_t, double2*,
+                                      double2*, int, cudaStream_t);
+template void launch_ts_update<float2>(const float2*, int, const double2*, double, float2*, int,
+                                       int64_t, cudaStream_t);
+template void launch_ts_update<double2>(const double2*, int, const double2*, double, double2*, int,
+                                        int64_t, cudaStream_t);
+template void launch_ts_trsm<float2>(float2*, int, int64_t, const double2*, cudaStream_t);
+template void launch_ts_trsm<double2>(double2*, int, int64_t, const double2*, cudaStream_t);

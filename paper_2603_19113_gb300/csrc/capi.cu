@@ -11,7 +11,6 @@
 #include <unordered_map>
 #include <vector>
 
-#include <cublas_v2.h>
 
 #include "common.cuh"
 #include "sbuild.cuh"
@@ -79,8 +78,6 @@ struct mbs_ctx {
     RhsBody* d_rhsb = nullptr;
     std::map<std::pair<int64_t, int>, int*> split_cache;  // (targets, nsplit) -> split_body
 
-    // cuBLAS handle for the tall-skinny GEMMs of block GMRES (created lazily)
-    cublasHandle_t blas = nullptr;
 
     // live timing of the G_hat kernels (mbs_profile)
     bool profile = false;
@@ -553,61 +550,13 @@ GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol
 // Block GMRES: the nrhs right-hand sides share one block Krylov space
 // span{R0, A R0, A^2 R0, ...} (each step applies the operator to an N x s
 // block, exactly like the lockstep GMRES, but every RHS minimises over all
-// s*j directions).  Block classical Gram-Schmidt applied twice with cuBLAS
-// GEMMs on the [s][N] blocks; the new block is orthonormalised by CholQR2
+// s*j directions).  Block classical Gram-Schmidt applied twice with the
+// tall-skinny kernels of blas.cu (fixed reduction order, so a solve is bitwise
+// reproducible next to other work); the new block is orthonormalised by CholQR2
 // (Gram matrix and Cholesky on the host in FP64, triangular solve on the
 // device); the block upper Hessenberg least-squares problem is reduced by
 // Givens rotations on the host in FP64.
 // ---------------------------------------------------------------------------
-template <typename V>
-struct Blas;
-template <>
-struct Blas<float2> {
-    using C = cuComplex;
-    static C make(double re, double im) { return make_cuComplex((float)re, (float)im); }
-    static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
-                               int k, C alpha, const float2* A, int lda, const float2* B, int ldb, C beta,
-                               float2* Cm, int ldc) {
-        return cublasCgemm(h, ta, tb, m, n, k, &alpha, (const C*)A, lda, (const C*)B, ldb, &beta,
-                           (C*)Cm, ldc);
-    }
-    static cublasStatus_t trsm_ru(cublasHandle_t h, int m, int n, const float2* R, float2* B) {
-        const C one = make(1.0, 0.0);
-        return cublasCtrsm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
-                           CUBLAS_DIAG_NON_UNIT, m, n, &one, (const C*)R, n, (C*)B, m);
-    }
-};
-template <>
-struct Blas<double2> {
-    using C = cuDoubleComplex;
-    static C make(double re, double im) { return make_cuDoubleComplex(re, im); }
-    static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
-                               int k, C alpha, const double2* A, int lda, const double2* B, int ldb, C beta,
-                               double2* Cm, int ldc) {
-        return cublasZgemm(h, ta, tb, m, n, k, &alpha, (const C*)A, lda, (const C*)B, ldb, &beta,
-                           (C*)Cm, ldc);
-    }
-    static cublasStatus_t trsm_ru(cublasHandle_t h, int m, int n, const double2* R, double2* B) {
-        const C one = make(1.0, 0.0);
-        return cublasZtrsm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
-                           CUBLAS_DIAG_NON_UNIT, m, n, &one, (const C*)R, n, (C*)B, m);
-    }
-};
-
-#define MBS_BLAS_TRY(call)                                                                   \
-    do {                                                                                     \
-        cublasStatus_t s_ = (call);                                                          \
-        if (s_ != CUBLAS_STATUS_SUCCESS)                                                     \
-            throw MbsError{MBS_ERR_CUDA, std::string(#call) + ": cuBLAS status " + std::to_string((int)s_)}; \
-    } while (0)
-
-cublasHandle_t blas_handle(mbs_ctx* c) {
-    if (!c->blas) MBS_BLAS_TRY(cublasCreate(&c->blas));
-    MBS_BLAS_TRY(cublasSetStream(c->blas, c->st));
-    MBS_BLAS_TRY(cublasSetPointerMode(c->blas, CUBLAS_POINTER_MODE_HOST));
-    return c->blas;
-}
-
 template <typename V>
 void to_host_cd(const V* d, size_t n, std::vector<cd>& out, cudaStream_t st) {
     std::vector<V> h(n);
@@ -650,18 +599,18 @@ bool chol_upper(const std::vector<cd>& G, int s, std::vector<cd>& R) {
 // W (N x s, [s][N]) = Q R with Q orthonormal: two Cholesky-QR passes.
 // Returns false on (numerical) rank deficiency.
 template <typename V>
-bool cholqr2(mbs_ctx* c, cublasHandle_t h, V* W, int64_t N, int s, V* d_small, std::vector<cd>& R) {
+bool cholqr2(mbs_ctx* c, V* W, int64_t N, int s, double2* d_small, double2* d_part,
+             std::vector<cd>& R) {
     std::vector<cd> G, R1, R2;
-    std::vector<V> stage;
-    using B = Blas<V>;
+    std::vector<double2> stage;
+    const int nb = ts_gram_blocks(N, s, s);
     for (int pass = 0; pass < 2; ++pass) {
-        MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, s, s, (int)N, B::make(1, 0), W, (int)N, W,
-                             (int)N, B::make(0, 0), d_small, s));
+        launch_ts_gram<V>(W, s, W, s, N, d_small, d_part, nb, c->st);
         to_host_cd(d_small, (size_t)s * s, G, c->st);
         std::vector<cd>& Rp = pass == 0 ? R1 : R2;
         if (!chol_upper(G, s, Rp)) return false;
         from_host_cd(Rp, d_small, c->st, stage);
-        MBS_BLAS_TRY(B::trsm_ru(h, (int)N, s, d_small, W));
+        launch_ts_trsm<V>(W, s, N, d_small, c->st);
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
     }
     // R = R2 R1
@@ -678,18 +627,23 @@ bool cholqr2(mbs_ctx* c, cublasHandle_t h, V* W, int64_t N, int s, V* d_small, s
 template <typename V>
 GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, int restart,
                   int maxit, bool verify) {
-    using B = Blas<V>;
     const int64_t N = c->N;
     const size_t NV = (size_t)s * N;
     GmresStats S;
     S.relres.assign(s, 0.0);
-    cublasHandle_t h = blas_handle(c);
     const std::string sfx = sizeof(V) == 8 ? "32" : "64";
     V* basis = scratch<V>(c, "bg_basis" + sfx, (size_t)(restart + 1) * NV);
     V* w = scratch<V>(c, "gm_w" + sfx, NV);
     V* r = scratch<V>(c, "gm_r" + sfx, NV);
-    V* d_h = scratch<V>(c, "bg_h" + sfx, (size_t)(restart + 1) * s * s);
-    V* d_small = scratch<V>(c, "bg_small" + sfx, (size_t)s * s);
+    double2* d_h = scratch<double2>(c, "bg_h", (size_t)(restart + 1) * s * s);
+    double2* d_small = scratch<double2>(c, "bg_small", (size_t)s * s);
+    // partial sums of the Gram products (nblk * ka * s for every block width ka used)
+    size_t part = 0;
+    for (int j = 0; j < restart; ++j) {
+        const int ka = (j + 1) * s;
+        part = std::max(part, (size_t)ts_gram_blocks(N, ka, s) * ka * s);
+    }
+    double2* d_part = scratch<double2>(c, "bg_part", part);
     double* d_inv = scratch<double>(c, "gm_inv", s);
     const std::vector<double> bn = norms<V>(c, b, s);
     if (x_zero) {
@@ -703,7 +657,6 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
     const int M = restart * s;         // columns of the block Hessenberg
     const int ldH = (restart + 1) * s;  // its rows
     std::vector<cd> H, G, Hcol, Rk, cs_, sn_;
-    std::vector<V> stage;
     double prev_worst = 1e300;
     while (true) {
         const std::vector<double> beta = norms<V>(c, r, s);
@@ -728,7 +681,7 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         MBS_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), s * sizeof(double), cudaMemcpyHostToDevice, c->st));
         launch_scale<V>(r, d_inv, basis, N, s, c->st);
         std::vector<cd> Rq;
-        if (!cholqr2<V>(c, h, basis, N, s, d_small, Rq)) break;  // R0 numerically rank deficient
+        if (!cholqr2<V>(c, basis, N, s, d_small, d_part, Rq)) break;  // R0 numerically rank deficient
         H.assign((size_t)ldH * M, cd(0.0));
         G.assign((size_t)ldH * s, cd(0.0));  // right-hand side of the small LS, column-major ldH
         for (int q = 0; q < s; ++q)
@@ -745,17 +698,15 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             // block CGS2: Hcol = V^H W; W -= V Hcol (twice)
             Hcol.assign((size_t)K * s, cd(0.0));
             for (int pass = 0; pass < 2; ++pass) {
-                MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, K, s, (int)N, B::make(1, 0), basis,
-                                     (int)N, w, (int)N, B::make(0, 0), d_h, K));
-                MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, s, K, B::make(-1, 0), basis,
-                                     (int)N, d_h, K, B::make(1, 0), w, (int)N));
+                launch_ts_gram<V>(basis, K, w, s, N, d_h, d_part, ts_gram_blocks(N, K, s), c->st);
+                launch_ts_update<V>(basis, K, d_h, -1.0, w, s, N, c->st);
                 std::vector<cd> hp;
                 to_host_cd(d_h, (size_t)K * s, hp, c->st);
                 for (size_t e = 0; e < hp.size(); ++e) Hcol[e] += hp[e];
             }
             V* vn = basis + (size_t)(j + 1) * NV;
             MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
-            if (!cholqr2<V>(c, h, vn, N, s, d_small, Rk)) {
+            if (!cholqr2<V>(c, vn, N, s, d_small, d_part, Rk)) {
                 breakdown = true;  // the new block adds no direction: the solution is in the space
                 Rk.assign((size_t)s * s, cd(0.0));
             }
@@ -816,10 +767,10 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
                 Y[(size_t)q * Mj + i] = std::abs(dgl) > 0 ? sum / dgl : cd(0.0);
             }
         if (Mj > 0) {
-            V* d_y = scratch<V>(c, "bg_y" + sfx, (size_t)M * s);
+            double2* d_y = scratch<double2>(c, "bg_y", (size_t)M * s);
+            std::vector<double2> stage;
             from_host_cd(Y, d_y, c->st, stage);
-            MBS_BLAS_TRY(B::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, s, Mj, B::make(1, 0), basis,
-                                 (int)N, d_y, Mj, B::make(1, 0), x, (int)N));
+            launch_ts_update<V>(basis, Mj, d_y, 1.0, x, s, N, c->st);
         }
         bool est_conv = true;
         for (int q = 0; q < s; ++q) est_conv = est_conv && S.relres[q] <= tol;
@@ -861,9 +812,11 @@ GmresStats krylov(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double to
 void validate_options(const mbs_options& o) {
     if (o.precision != MBS_PREC_FP64 && o.precision != MBS_PREC_MIXED && o.precision != MBS_PREC_FP32)
         throw MbsError{MBS_ERR_ARG, "precision must be MBS_PREC_FP64, MBS_PREC_MIXED or MBS_PREC_FP32"};
-    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.restart < 1 || o.max_iter < 1 || o.max_sweeps < 1 ||
+    if (!(o.tol > 0) || !(o.inner_tol > 0) || o.restart < 1 || o.restart > 1800 || o.max_iter < 1 || o.max_sweeps < 1 ||
         !(o.ls_rcond > 0 && o.ls_rcond < 1))
         throw MbsError{MBS_ERR_ARG, "invalid tolerance / restart / iteration options"};
+    if (o.mac_path < 0 || o.mac_path > 3)
+        throw MbsError{MBS_ERR_ARG, "mac_path must be 0, 1, 2 or 3"};
 }
 
 template <typename F>
@@ -1315,7 +1268,6 @@ void mbs_destroy(mbs_ctx* c) {
         for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
         for (auto& kv : c->bufs) dfree(c, kv.second.p);
         c->bufs.clear();
-        if (c->blas) cublasDestroy(c->blas);
         if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     }
     delete c;

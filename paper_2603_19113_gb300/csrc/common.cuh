@@ -129,6 +129,19 @@ void launch_sub64(const double2* b, const double2* ax, double2* r, int64_t N, in
 template <typename V>
 void launch_sub(const V* b, const V* ax, V* r, int64_t n, cudaStream_t st);
 void launch_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t st);
+// Tall-skinny block products of block GMRES (fixed reduction order):
+// C = A^H B (ka x kb, column-major, FP64), B += alpha A H, B <- B R^{-1}
+// (R upper triangular, FP64).  ts_gram needs scratch of nblk * ka * kb
+// double2 with nblk = ts_gram_blocks(N, ka, kb); kb <= 16 for update/trsm.
+int ts_gram_blocks(int64_t N, int ka, int kb);
+template <typename V>
+void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* C,
+                    double2* scratch, int nblk, cudaStream_t st);
+template <typename V>
+void launch_ts_update(const V* A, int ka, const double2* H, double alpha, V* B, int kb, int64_t N,
+                      cudaStream_t st);
+template <typename V>
+void launch_ts_trsm(V* B, int kb, int64_t N, const double2* R, cudaStream_t st);
 void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st);
 
 int mbs_num_sms();
