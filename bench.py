@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the served trace (0 = skip); body counts scaled to 20..300")
     ap.add_argument("--serve-tmax", type=int, default=300)
+    ap.add_argument("--mac", type=int, default=0,
+                    help="FP32 G_hat kernel (mac_path option): 0 auto (tcgen05), 1 FP32 pipe, "
+                         "2 mma.sync tensor-core multiply-add, 3 tcgen05 tensor-core multiply-add")
     ap.add_argument("--kernel", choices=["g32", "g64"], default=None,
                     help="only apply G_hat (FP32 or FP64) to 8 random vectors, steps times "
                          "(for profiling the dominant kernel); prints per-launch times")
@@ -110,7 +113,7 @@ def run_kernel_only(a):
 
     wl = mi.config1()
     stream = torch.cuda.current_stream()
-    ctx = pkg.Context(2, wl.kappa, stream=stream.cuda_stream)
+    ctx = pkg.Context(2, wl.kappa, stream=stream.cuda_stream, mac_path=a.mac)
     ctx.build_scattering_matrices(wl)
     q = torch.randn(wl.nrhs, ctx.N, dtype=torch.complex128, device="cuda").T
     prec = pkg.PREC_FP32 if a.kernel == "g32" else pkg.PREC_FP64
@@ -121,7 +124,8 @@ def run_kernel_only(a):
     for _ in range(a.steps):
         ctx.apply_G(q, prec)
     kt = ctx.kernel_times()
-    print(json.dumps({"kernel": a.kernel, "N": ctx.N, "nrhs": wl.nrhs, **kt}), flush=True)
+    print(json.dumps({"kernel": a.kernel, "mac_path": a.mac, "N": ctx.N, "nrhs": wl.nrhs, **kt}),
+          flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -337,7 +341,7 @@ def run_mbs(a, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=1e-6, restart=a.restart,
-                max_iter=50000, max_sweeps=12, stream=stream.cuda_stream)
+                max_iter=50000, max_sweeps=12, stream=stream.cuda_stream, mac_path=a.mac)
     ctx = pkg.Context(2, wl.kappa, **opts)
 
     def step(v, tg):
@@ -449,7 +453,8 @@ def run_mbs(a, ws, rank, local):
     flops_launch = pairs_mv * FLOPS_PER_PAIR_2D(nrhs)
     avg_ms = kt["g32_ms"] / max(1, kt["g32_launches"])
     achieved = flops_launch / (avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "g_f32_kernel<2,8>", "achieved": achieved,
+    kname = {1: "g_f32_kernel<2,8,2>", 2: "g_tc_kernel<2,1>"}.get(a.mac, "g_umma_kernel<2,8>")
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": None, "avg_launch_ms": avg_ms, "launches": kt["g32_launches"],
                 "flops_per_launch": flops_launch,

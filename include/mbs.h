@@ -68,7 +68,7 @@ typedef struct mbs_options {
     int precision;       /* MBS_PREC_FP64 or MBS_PREC_MIXED (solve); apply calls accept FP32 too */
     double tol;          /* stop when ||b - A q||_2 / ||b||_2 <= tol for every RHS (FP64 residual) */
     double inner_tol;    /* mixed precision: relative residual target of each FP32 inner solve */
-    int restart;         /* GMRES restart length (Krylov vectors kept per RHS) */
+    int restart;         /* GMRES restart length (Krylov vectors kept per RHS), 1..1800 */
     int max_iter;        /* cap on Arnoldi steps summed over the whole solve */
     int max_sweeps;      /* mixed precision: cap on refinement sweeps */
     double ls_rcond;     /* relative truncation of the least-squares solves in the S build */
@@ -76,7 +76,7 @@ typedef struct mbs_options {
     size_t hbm_budget;   /* bytes of device memory the context may hold (0 = no cap) */
     int tile_override;   /* 0 = tuned launch shape; >0 forces the source-split count of G_hat */
     int block_krylov;    /* 1 (default): several right-hand sides share one block Krylov space; 0: independent GMRES in lockstep */
-    int mac_path;        /* FP32 G_hat multiply-add: 0 auto (the faster, currently the FP32 pipe), 1 FP32 pipe, 2 tensor cores (3xTF32 mma.sync) */
+    int mac_path;        /* FP32 G_hat kernel: 0 auto (3 for >= 4 RHS, else 1), 1 FP32 pipe, 2 mma.sync tensor-core multiply-add (3xTF32), 3 tcgen05 tensor-core multiply-add (3xTF32, accumulators in tensor memory) */
 } mbs_options;
 
 typedef struct mbs_shape {
@@ -199,7 +199,8 @@ mbs_status mbs_inject_scattering(mbs_ctx* ctx, int shape, int k, const int* skel
 
 /* Measure device peaks with short microbenchmarks: out[0] FP32 FMA TFLOP/s,
  * out[1] FP64 FMA TFLOP/s, out[2] MUFU (sin+cos+rsqrt) Tops/s, out[3] SM
- * count, out[4] SM clock kHz.  Runs on the current device. */
+ * count, out[4] SM clock kHz, out[5] FP32 TFLOP/s with packed f32x2 FMAs.
+ * out must hold 6 doubles.  Runs on the current device. */
 mbs_status mbs_measure_peaks(double* out);
 
 /*

@@ -309,12 +309,12 @@ Context.kernel_times = _ctx_kernel_times
 
 
 def measure_peaks() -> dict:
-    out = (C.c_double * 5)()
+    out = (C.c_double * 6)()
     st = _lib().mbs_measure_peaks(out)
     if st != L.MBS_OK:
         raise MbsError(st, "mbs_measure_peaks")
     return {"fp32_tflops": out[0], "fp64_tflops": out[1], "mufu_tops": out[2], "sms": int(out[3]),
-            "clock_khz": int(out[4])}
+            "clock_khz": int(out[4]), "fp32x2_tflops": out[5]}
 
 
 class Server:

@@ -17,13 +17,14 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmbs.so")
-SOURCES = ["capi.cu", "gmatvec.cu", "blas.cu", "sbuild.cu", "peaks.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "gmatvec.cu", "gumma.cu", "blas.cu", "sbuild.cu", "peaks.cu", "serve.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-diag-suppress", "177"]
 # single-precision G_hat kernels: flush denormals, approximate division / square
 # root (these flags touch FP32 arithmetic only; the FP64 kernels are unaffected)
-EXTRA = {"gmatvec.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
+EXTRA = {f: ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"] for f in ("gmatvec.cu", "gumma.cu")}
 
 
 def _nvcc() -> str:

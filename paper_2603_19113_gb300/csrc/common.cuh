@@ -85,16 +85,39 @@ void launch_pair_table(int dim, int T, const double* d_centres, const double* d_
                        double kappa, float4* pair, float* pair_phi0, cudaStream_t st);
 // ev0/ev1 (nullable) are recorded on st around the G_hat kernel launches
 // (not the split reduction), for live timing of the dominant kernel.
-// mac_path: 0 auto (FP32 pipe, measured faster), 1 FP32 pipe, 2 tensor cores.
+// mac_path: 0 auto (FP32 pipe), 1 FP32 pipe, 2 mma.sync tensor-core
+// multiply-add, 3 tcgen05 tensor-core multiply-add (needs U).
+struct UmmaLayout;
 void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, float2* y,
                   float2* part, int nsplit, const int* d_split_body, cudaStream_t st,
-                  cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int mac_path = 0);
+                  cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int mac_path = 0,
+                  const UmmaLayout* U = nullptr);
 void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
                       const double2* q, double2* u, double2* part, int nsplit,
                       const int* d_split_body, cudaStream_t st);
+
+// Tensor-core FP32 G_hat (gumma.cu).  Sources are taken in chunks of
+// umma_chunk() that never straddle a body: chunk_off[T+1] (prefix sums of
+// ceil(k_tau / umma_chunk())) and
+// chunk_body[nchunks]; pack holds one record per chunk (umma_pack_bytes);
+// err is set to 1 if a bounded wait of the kernel ran out.  part holds
+// nsplit * nrhs * N values for tiles of umma_tile() targets.
+struct UmmaLayout {
+    int64_t nchunks;
+    const int* chunk_off;
+    const int* chunk_body;
+    unsigned char* pack;
+    size_t pack_bytes;
+    int* err;
+};
+size_t umma_pack_bytes(int64_t nchunks, int nrhs);
+int umma_tile();
+int umma_chunk();
+void launch_G_umma(const GLayout& L, const UmmaLayout& U, double kappa, int nrhs, const float2* q,
+                   float2* part, int nsplit, const int* d_split_body, cudaStream_t st);
 
 // S application and vector kernels (blas.cu)
 struct SBlocks {

@@ -1,5 +1,6 @@
 // Short microbenchmarks of the device's arithmetic peaks, the denominators of
-// the roofline fractions: FP32 FMA, FP64 FMA and MUFU (sin + cos + rsqrt).
+// the roofline fractions: FP32 FMA (scalar and packed f32x2), FP64 FMA and
+// MUFU (sin + cos + rsqrt).
 #include <cstring>
 
 #include "common.cuh"
@@ -17,6 +18,33 @@ __global__ void fma32_kernel(float* out, float a, float b) {
         x4 = fmaf(x4, a, b); x5 = fmaf(x5, a, b); x6 = fmaf(x6, a, b); x7 = fmaf(x7, a, b);
     }
     const float s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    if (s == 12345.678f) out[0] = s;
+}
+
+// Packed FP32: one fma.rn.f32x2 performs two independent FMAs (sm_100 family).
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__global__ void fma32x2_kernel(float* out, float a, float b) {
+    const float x = threadIdx.x * 1e-3f;
+    unsigned long long x0 = pack2(x, x + 1.f), x1 = pack2(x + 2.f, x + 3.f);
+    unsigned long long x2 = pack2(x + 4.f, x + 5.f), x3 = pack2(x + 6.f, x + 7.f);
+    const unsigned long long aa = pack2(a, a), bb = pack2(b, b);
+#pragma unroll 16
+    for (int i = 0; i < PK_ITERS; ++i) {
+        asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x0) : "l"(aa), "l"(bb));
+        asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x1) : "l"(aa), "l"(bb));
+        asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x2) : "l"(aa), "l"(bb));
+        asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x3) : "l"(aa), "l"(bb));
+    }
+    float s = 0.f;
+    for (unsigned long long v : {x0, x1, x2, x3}) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+        s += lo + hi;
+    }
     if (s == 12345.678f) out[0] = s;
 }
 
@@ -78,6 +106,7 @@ extern "C" mbs_status mbs_measure_peaks(double* out) {
     const float t32 = time_kernel([&] { fma32_kernel<<<blocks, threads>>>(d32, 0.999f, 1e-3f); });
     const float t64 = time_kernel([&] { fma64_kernel<<<blocks, threads>>>(d64, 0.999, 1e-3); });
     const float tmu = time_kernel([&] { mufu_kernel<<<blocks, threads>>>(d32); });
+    const float t2 = time_kernel([&] { fma32x2_kernel<<<blocks, threads>>>(d32, 0.999f, 1e-3f); });
     const cudaError_t e = cudaDeviceSynchronize();
     cudaFree(d32);
     cudaFree(d64);
@@ -87,5 +116,6 @@ extern "C" mbs_status mbs_measure_peaks(double* out) {
     out[2] = thr * (PK_ITERS / 4) * 3 / (tmu * 1e-3) / 1e12;       // MUFU Tops/s
     out[3] = sms;
     out[4] = khz;
+    out[5] = thr * PK_ITERS * 8 * 2 / (t2 * 1e-3) / 1e12;         // FP32 TFLOP/s, f32x2
     return MBS_OK;
 }

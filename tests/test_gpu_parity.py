@@ -72,12 +72,13 @@ def test_G_2d_fp64_and_fp32(pkg, nrhs):
     assert _nrel(y32, ref) < 2e-5
 
 
-@pytest.mark.parametrize("mac_path", [1, 2])
-@pytest.mark.parametrize("dim,nrhs", [(2, 8), (2, 5), (2, 16), (3, 8), (3, 11)])
+@pytest.mark.parametrize("mac_path", [1, 2, 3])
+@pytest.mark.parametrize("dim,nrhs", [(2, 8), (2, 5), (2, 16), (2, 1), (3, 8), (3, 11), (3, 2)])
 def test_G_fp32_multiply_add_paths(pkg, mac_path, dim, nrhs):
-    """Both FP32 multiply-add paths (FP32 pipe; tensor cores with the 3xTF32
-    split) against the oracle, with right-hand-side counts that fill, pad and
-    span two tensor-core blocks."""
+    """Every FP32 G_hat kernel (FP32 pipe; mma.sync and tcgen05 tensor-core
+    multiply-add with the 3xTF32 split) against the oracle, with right-hand-side
+    counts that fill, pad and span two blocks of right-hand sides (fewer than 4
+    right-hand sides take the FP32 pipe on every path)."""
     wl = (mi.tiny_2d(seed=4, T=9, kappa=6.0, ks=(24, 37, 50)) if dim == 2
           else mi.tiny_3d(seed=1, T=5, kappa=3.0, nth=10, nph=14, p=141, k=70))
     ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, mac_path=mac_path)
@@ -86,15 +87,16 @@ def test_G_fp32_multiply_add_paths(pkg, mac_path, dim, nrhs):
     assert _nrel(ctx.apply_G(q, pkg.PREC_FP32), ref) < 2e-5
 
 
-def test_G_2d_small_arguments(pkg):
+@pytest.mark.parametrize("mac_path", [1, 3])
+def test_G_2d_small_arguments(pkg, mac_path):
     """Neighbouring bodies at low kappa put kappa r below 3 and between 3 and
     16: every branch of the H0 evaluation is exercised."""
     wl = mi.tiny_2d(seed=2, T=9, kappa=2.0, ks=(30, 41), spacing=2.9)
-    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, mac_path=mac_path)
     x = wl.kappa * np.linalg.norm(lay["xhat"][:, None] - lay["xhat"][None], axis=2)
     other = lay["body"][:, None] != lay["body"][None, :]
     assert x[other].min() < 3.0 and x[other].max() > 16.0
-    q = _rand((ctx.N, 2), 7)
+    q = _rand((ctx.N, 5), 7)
     ref = orc.G_dense(2, wl.kappa, lay["xhat"], lay["body"]) @ q
     assert _rel(ctx.apply_G(q, pkg.PREC_FP64), ref) < 1e-12
     assert _nrel(ctx.apply_G(q, pkg.PREC_FP32), ref) < 2e-5
@@ -120,20 +122,21 @@ def test_apply_operator_matches_oracle(pkg):
     assert _nrel(ctx.apply_operator(q), ref) < 2e-5
 
 
-def test_G_full_size_config1_sampled_rows(pkg):
+@pytest.mark.parametrize("mac_path", [0, 3])
+def test_G_full_size_config1_sampled_rows(pkg, mac_path):
     """The bench workload (1000 bodies, N = 64,000, 8 right-hand sides, kappa = 40)
-    in the bench's launch configuration: 256 sampled rows against the oracle."""
+    in the bench's launch configuration: 256 sampled rows against the oracle.
+    The skeleton is the oracle's (injected), so no oracle input comes from the
+    GPU."""
     wl = mi.config1()
-    ctx = pkg.Context(2, wl.kappa)
-    ctx.build_scattering_matrices(wl)
-    N, off, xyz = ctx.get_layout()
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, mac_path=mac_path)
+    N = ctx.N
     assert N == 64000
-    body = np.repeat(np.arange(wl.T), np.diff(off))
     q = _rand((N, 8), 5)
     y64 = ctx.apply_G(q, pkg.PREC_FP64)
     y32 = ctx.apply_G(q, pkg.PREC_FP32)
     rows = np.random.default_rng(0).choice(N, 256, replace=False)
-    ref = orc.G_rows(2, wl.kappa, xyz, body, q, rows)
+    ref = orc.G_rows(2, wl.kappa, lay["xhat"], lay["body"], q, rows)
     assert _rel(y64[rows], ref) < 1e-12
     assert _nrel(y32[rows], ref) < 2e-5
 
