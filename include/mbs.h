@@ -77,6 +77,9 @@ typedef struct mbs_options {
     int tile_override;   /* 0 = tuned launch shape; >0 forces the source-split count of G_hat */
     int block_krylov;    /* 1 (default): several right-hand sides share one block Krylov space; 0: independent GMRES in lockstep */
     int mac_path;        /* FP32 G_hat kernel: 0 auto (3 for >= 4 RHS, else 1), 1 FP32 pipe, 2 mma.sync tensor-core multiply-add (3xTF32), 3 tcgen05 tensor-core multiply-add (3xTF32, accumulators in tensor memory) */
+    int autotune;        /* 1 (default): the first FP32 G_hat matvec of a problem class times the candidate
+                            launch shapes (kernel path x source-split count) and the fastest is reused process-wide;
+                            0: heuristic shape */
 } mbs_options;
 
 typedef struct mbs_shape {
@@ -110,7 +113,8 @@ typedef struct mbs_solve_info {
 typedef struct mbs_ctx mbs_ctx;
 
 /* Fill *opt with defaults: FP64, tol 1e-11, inner_tol 1e-6, restart 60,
- * max_iter 20000, max_sweeps 8, ls_rcond 1e-14, stream NULL, no budget. */
+ * max_iter 20000, max_sweeps 8, ls_rcond 1e-14, stream NULL, no budget,
+ * automatic G_hat kernel, autotuning on. */
 void mbs_default_options(mbs_options* opt);
 
 /* Create a context for dimension dim (2 or 3) and wavenumber kappa > 0
@@ -192,7 +196,10 @@ mbs_status mbs_evaluate_field(mbs_ctx* ctx, int nrhs, int64_t M, const double* p
  * computed data (e.g. the CPU reference), isolating the global solve.
  * skel: k indices into the shape's collocation points; S: k x k complex;
  * W: k x m complex (b_tau = W v_tau), or NULL to keep the built right-hand
- * side operator.  Skeleton coordinates are recomputed for every body.
+ * side operator (if the skeleton changes without W, mbs_rhs then fails with
+ * MBS_ERR_STATE).  The skeleton coordinates of every body are recomputed once,
+ * by the next call that uses the layout, so many shapes can be injected in a
+ * row at the cost of one layout rebuild.
  */
 mbs_status mbs_inject_scattering(mbs_ctx* ctx, int shape, int k, const int* skel,
                                  const double* S, const double* W);

@@ -262,9 +262,19 @@ class Context:
         self._check(_lib().mbs_inject_scattering(
             self._h, shape, len(skel), skel.ctypes.data_as(C.POINTER(C.c_int)),
             C.c_void_p(Sf.ctypes.data), None if Wf is None else C.c_void_p(Wf.ctypes.data)))
-        N = C.c_int64()
-        self._check(_lib().mbs_get_layout(self._h, C.byref(N), None, None))
-        self.N = int(N.value)
+        self._N = None  # the library rebuilds the layout on its next use
+
+    @property
+    def N(self) -> int:
+        if self._N is None:
+            n = C.c_int64()
+            self._check(_lib().mbs_get_layout(self._h, C.byref(n), None, None))
+            self._N = int(n.value)
+        return self._N
+
+    @N.setter
+    def N(self, v):
+        self._N = v
 
 
 def apply_G_noalloc(dim: int, kappa: float, body_offsets, body, xw, q, y, stream=None) -> None:

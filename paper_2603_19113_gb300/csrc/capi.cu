@@ -34,6 +34,7 @@ struct ShapeHost {
     int k = 0, rankA = 0, rankB = 0;
     double eps_ach = 0;
     std::vector<int> skel;
+    bool rhs_ok = true;  // false after a skeleton was injected without its W
     // device (owned by the context allocation list)
     double *dx = nullptr, *dy = nullptr, *dz = nullptr;
     double2 *AU = nullptr, *diagA = nullptr, *Zs = nullptr, *C = nullptr, *S64 = nullptr,
@@ -62,6 +63,7 @@ struct mbs_ctx {
     std::vector<int> kb;  // per-body skeleton count
     std::vector<double> skel_world;  // dim * N SoA
     bool built = false;
+    bool layout_dirty = false;  // injected scattering data not yet in the device layout
     int kmax = 0, mmax = 0, nmax = 0;
 
     // device layout
@@ -217,26 +219,34 @@ void finish_out(mbs_ctx* c, const OutBuf& o) {
     MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
 }
 
+void refresh_layout(mbs_ctx* c);
+
+// A built context with an up-to-date device layout (injections are applied
+// lazily, so many shapes can be injected at the cost of one layout rebuild).
 void require_built(mbs_ctx* c) {
     if (!c->built) throw MbsError{MBS_ERR_STATE, "scattering matrices not built"};
+    if (c->layout_dirty) {
+        refresh_layout(c);
+        c->layout_dirty = false;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // launch-shape helpers
 // ---------------------------------------------------------------------------
+int max_nsplit(const mbs_ctx* c) { return std::max(1, std::min(c->T, 64)); }
+
 int choose_nsplit(mbs_ctx* c, int64_t ntargets) {
     if (c->opt.tile_override > 0) return std::min(c->opt.tile_override, std::max(1, c->T));
     const int64_t tiles = (ntargets + 255) / 256;
     const int64_t want = 16LL * mbs_num_sms();
     int64_t ns = (want + tiles - 1) / std::max<int64_t>(1, tiles);
-    ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::min(c->T, 64)));
+    ns = std::max<int64_t>(1, std::min<int64_t>(ns, max_nsplit(c)));
     return (int)ns;
 }
 
 // split_body[s] = first source body of split s, balanced by skeleton counts.
-int* split_for(mbs_ctx* c, int64_t ntargets, int* nsplit_out) {
-    const int ns = choose_nsplit(c, ntargets);
-    *nsplit_out = ns;
+int* split_table(mbs_ctx* c, int ns) {
     auto key = std::make_pair((int64_t)ns, 0);
     auto it = c->split_cache.find(key);
     if (it != c->split_cache.end()) return it->second;
@@ -253,6 +263,12 @@ int* split_for(mbs_ctx* c, int64_t ntargets, int* nsplit_out) {
     MBS_CUDA_TRY(cudaMemcpy(d, sb.data(), sb.size() * sizeof(int), cudaMemcpyHostToDevice));
     c->split_cache[key] = d;
     return d;
+}
+
+int* split_for(mbs_ctx* c, int64_t ntargets, int* nsplit_out) {
+    const int ns = choose_nsplit(c, ntargets);
+    *nsplit_out = ns;
+    return split_table(c, ns);
 }
 
 GLayout glayout(mbs_ctx* c) {
@@ -308,21 +324,37 @@ int* device_err(mbs_ctx* c) {
     return c->d_err;
 }
 
-// y = G_hat x (FP32)
-void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
-    const int path = g32_path(c, nrhs);
-    int ns;
-    // the tcgen05 kernel tiles 128 targets per CTA, the others 256
-    int* sb = split_for(c, path == 3 ? 2 * c->N : c->N, &ns);
-    float2* part = scratch<float2>(c, "part32", (size_t)ns * nrhs * c->N);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->profile) {
-        e0 = take_event(c);
-        e1 = take_event(c);
-        c->ev32.emplace_back(e0, e1);
-    }
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner of the FP32 G_hat matvec.  The first FP32 matvec of a
+// problem class (device, dimension, right-hand sides, kernel option and the
+// power-of-two buckets of N and of the body count) times every candidate
+// shape on the caller's own data: the kernel path (tcgen05 or FP32 pipe,
+// unless mac_path fixes it) times the source-split count (the heuristic's,
+// half and double).  The fastest is kept in a process-wide table, so every
+// later matvec of that class, in any context, uses the same shape; a solve
+// therefore gives the same result alone and next to other solves.
+// mbs_options.autotune = 0 (or a tile_override) keeps the heuristic shape.
+// ---------------------------------------------------------------------------
+struct Shape32 {
+    int path;
+    int nsplit;
+};
+
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, Shape32> g_tune;
+
+int log2_bucket(int64_t v) {
+    int b = 0;
+    while ((int64_t(1) << b) < v) ++b;
+    return b;
+}
+
+void launch_g32(mbs_ctx* c, int nrhs, const float2* x, float2* y, const Shape32& sh,
+                cudaEvent_t e0, cudaEvent_t e1) {
+    int* sb = split_table(c, sh.nsplit);
+    float2* part = scratch<float2>(c, "part32", (size_t)sh.nsplit * nrhs * c->N);
     UmmaLayout U{};
-    if (path == 3) {
+    if (sh.path == 3) {
         U.nchunks = c->nchunks;
         U.chunk_off = c->d_chunk_off;
         U.chunk_body = c->d_chunk_body;
@@ -330,8 +362,76 @@ void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
         U.pack = scratch<unsigned char>(c, "umma_pack", U.pack_bytes);
         U.err = device_err(c);
     }
-    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st, e0, e1, path,
-                 path == 3 ? &U : nullptr);
+    launch_G_f32(glayout(c), c->kappa, nrhs, x, y, part, sh.nsplit, sb, c->st, e0, e1, sh.path,
+                 sh.path == 3 ? &U : nullptr);
+}
+
+Shape32 heuristic_shape32(mbs_ctx* c, int nrhs) {
+    Shape32 sh;
+    sh.path = g32_path(c, nrhs);
+    // the tcgen05 kernel tiles 128 targets per CTA, the others 256
+    sh.nsplit = choose_nsplit(c, sh.path == 3 ? 2 * c->N : c->N);
+    return sh;
+}
+
+Shape32 shape32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
+    const Shape32 h = heuristic_shape32(c, nrhs);
+    if (!c->opt.autotune || c->opt.tile_override > 0) return h;
+    int dev = 0;
+    MBS_CUDA_TRY(cudaGetDevice(&dev));
+    const std::array<int, 6> key{dev, c->dim, nrhs, c->opt.mac_path, log2_bucket(c->N), log2_bucket(c->T)};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+        Shape32 sh = it->second;
+        sh.nsplit = std::min(sh.nsplit, max_nsplit(c));
+        return sh;
+    }
+    std::vector<Shape32> cand;
+    std::vector<int> paths{h.path};
+    if (c->opt.mac_path == 0 && h.path == 3) paths.push_back(1);
+    for (int p : paths) {
+        const int base = choose_nsplit(c, p == 3 ? 2 * c->N : c->N);
+        for (int ns : {base, base / 2, 2 * base}) {
+            ns = std::max(1, std::min(ns, max_nsplit(c)));
+            bool dup = false;
+            for (const Shape32& q : cand) dup = dup || (q.path == p && q.nsplit == ns);
+            if (!dup) cand.push_back({p, ns});
+        }
+    }
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    Shape32 best = h;
+    float best_ms = 0.f;
+    launch_g32(c, nrhs, x, y, cand[0], nullptr, nullptr);  // warm-up
+    for (size_t ci = 0; ci < cand.size(); ++ci) {
+        MBS_CUDA_TRY(cudaEventRecord(a, c->st));
+        launch_g32(c, nrhs, x, y, cand[ci], nullptr, nullptr);
+        MBS_CUDA_TRY(cudaEventRecord(b, c->st));
+        MBS_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        MBS_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (ci == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = cand[ci];
+        }
+    }
+    c->ev_pool.push_back(a);
+    c->ev_pool.push_back(b);
+    g_tune[key] = best;
+    return best;
+}
+
+// y = G_hat x (FP32); a first call of a problem class may run the autotuner,
+// whose last timed launch is overwritten by the final one below.
+void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
+    const Shape32 sh = shape32(c, nrhs, x, y);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        c->ev32.emplace_back(e0, e1);
+    }
+    launch_g32(c, nrhs, x, y, sh, e0, e1);
 }
 void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
     int ns;
@@ -1248,6 +1348,7 @@ void mbs_default_options(mbs_options* o) {
     o->tile_override = 0;
     o->block_krylov = 1;
     o->mac_path = 0;
+    o->autotune = 1;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {
@@ -1397,6 +1498,9 @@ mbs_status mbs_rhs(mbs_ctx* c, int nrhs, const double* v, double* b) {
     return guarded(c, [&]() {
         require_built(c);
         if (nrhs < 1 || !v || !b) throw MbsError{MBS_ERR_ARG, "bad nrhs or null pointer"};
+        for (const mbs_body& B : c->bodies)
+            if (!c->shapes[B.shape].rhs_ok)
+                throw MbsError{MBS_ERR_STATE, "a shape's skeleton was injected without its W"};
         const double2* dv = in_dev(c, v, (size_t)c->Mtot * nrhs, "io_v");
         OutBuf ob = out_dev(c, b, (size_t)c->N * nrhs, "io_b");
         launch_rhs(c->d_rhsb, c->T, nrhs, c->mmax, c->nmax, dv, c->Mtot, ob.dev, c->N, c->st);
@@ -1606,15 +1710,15 @@ mbs_status mbs_evaluate_field(mbs_ctx* c, int nrhs, int64_t M, const double* pts
 mbs_status mbs_inject_scattering(mbs_ctx* c, int shape, int k, const int* skel, const double* S,
                                  const double* W) {
     return guarded(c, [&]() {
-        require_built(c);
+        if (!c->built) throw MbsError{MBS_ERR_STATE, "scattering matrices not built"};
         if (shape < 0 || shape >= (int)c->shapes.size() || !c->shapes[shape].used)
             throw MbsError{MBS_ERR_ARG, "shape not built"};
         ShapeHost& s = c->shapes[shape];
         if (k < 1 || k > s.m || !skel || !S) throw MbsError{MBS_ERR_ARG, "bad k / skel / S"};
         for (int i = 0; i < k; ++i)
             if (skel[i] < 0 || skel[i] >= s.m) throw MbsError{MBS_ERR_ARG, "skeleton index out of range"};
-        if (!W && (k != s.k || !std::equal(skel, skel + k, s.skel.begin())))
-            throw MbsError{MBS_ERR_ARG, "W is required when the skeleton differs from the built one"};
+        const bool same = k == s.k && std::equal(skel, skel + k, s.skel.begin());
+        s.rhs_ok = W != nullptr || (same && s.rhs_ok);
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
         s.k = k;
         s.skel.assign(skel, skel + k);
@@ -1628,7 +1732,7 @@ mbs_status mbs_inject_scattering(mbs_ctx* c, int shape, int k, const int* skel, 
         } else {
             s.W = nullptr;
         }
-        refresh_layout(c);
+        c->layout_dirty = true;  // rebuilt by the next call that needs the layout
         return MBS_OK;
     });
 }

@@ -144,6 +144,41 @@ def test_G_full_size_config1_sampled_rows(pkg, mac_path):
 # --------------------------------------------------------------------------
 # right-hand side, solve, field
 # --------------------------------------------------------------------------
+def _inject_every_other_point(ctx, wl):
+    """Skeleton = every other collocation point of each shape, S = 0.  The
+    G_hat layout is then fixed by the inputs alone, so the oracle computes its
+    own skeleton coordinates and takes nothing from the GPU."""
+    sdata = []
+    for s, sh in enumerate(wl.shapes):
+        skel = np.arange(0, 2 * sh.k, 2, dtype=np.int32)
+        assert skel[-1] < sh.m
+        ctx.inject_scattering(s, skel, np.zeros((sh.k, sh.k), np.complex128))
+        sdata.append({"skel": skel})
+    return orc.layout(wl, sdata)
+
+
+@pytest.mark.parametrize("name,rows", [("config2", 24), ("config3", 96)])
+def test_G_full_size_sampled_rows_fp32(pkg, name, rows):
+    """The two largest workloads at full size in their launch configuration:
+    2D, 10,000 bodies of 35-105 skeleton points (ragged 16-point chunks),
+    N ~ 700k, 16 right-hand sides (one 16-column tcgen05 block); 3D, 2000
+    ellipsoids, N = 600,000, 4 right-hand sides (a padded 8-column block, or
+    the FP32 pipe where the autotuner finds it faster).  Sampled rows of the
+    FP32 G_hat against the oracle."""
+    wl = getattr(mi, name)()
+    ctx = pkg.Context(wl.dim, wl.kappa)
+    ctx.build_scattering_matrices(wl)
+    lay = _inject_every_other_point(ctx, wl)
+    N = ctx.N
+    assert N == lay["xhat"].shape[0] and N > 500_000
+    q = _rand((N, wl.nrhs), 9)
+    y32 = ctx.apply_G(q, pkg.PREC_FP32)
+    sel = np.random.default_rng(1).choice(N, rows, replace=False)
+    ref = orc.G_rows(wl.dim, wl.kappa, lay["xhat"], lay["body"], q, sel)
+    assert _nrel(y32[sel], ref) < 2e-5
+    ctx.close()
+
+
 def test_injected_solve_fp64_and_mixed_config0(pkg):
     wl = mi.config0()
     ref = orc.solve_workload(wl)
