@@ -269,6 +269,39 @@ __global__ void f64_to_f32_kernel(const double2* __restrict__ a, float2* __restr
 
 inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Cholesky G = R^H R of one s x s Hermitian matrix (column-major, s <= 16) in
+// FP64 by one thread: R upper triangular, zero below the diagonal.  *ok = 1
+// if every pivot exceeds 1e-13 times the largest diagonal entry of G;
+// otherwise *ok = 0 and R = I, so a triangular solve with it stays finite.
+__global__ void chol_small_kernel(const double2* __restrict__ G, int s, double2* __restrict__ R,
+                                  double* __restrict__ ok) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double gmax = 0.0;
+    for (int i = 0; i < s; ++i) gmax = fmax(gmax, G[(int64_t)i * s + i].x);
+    for (int e = 0; e < s * s; ++e) R[e] = make_double2(0.0, 0.0);
+    bool good = true;
+    for (int j = 0; j < s && good; ++j) {
+        for (int i = 0; i <= j; ++i) {
+            double2 sum = G[(int64_t)j * s + i];  // G(i, j)
+            for (int k = 0; k < i; ++k)
+                sum = csub(sum, cmulc(R[(int64_t)i * s + k], R[(int64_t)j * s + k]));
+            if (i == j) {
+                if (!(sum.x > 1e-13 * gmax)) {
+                    good = false;
+                    break;
+                }
+                R[(int64_t)j * s + j] = make_double2(sqrt(sum.x), 0.0);
+            } else {
+                const double d = R[(int64_t)i * s + i].x;
+                R[(int64_t)j * s + i] = make_double2(sum.x / d, sum.y / d);
+            }
+        }
+    }
+    if (!good)
+        for (int e = 0; e < s * s; ++e) R[e] = make_double2((e % (s + 1)) == 0 ? 1.0 : 0.0, 0.0);
+    *ok = good ? 1.0 : 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // Tall-skinny products of block GMRES.  A block of k vectors of length N is
 // stored [k][N].  Every reduction runs in a fixed order, so a solve returns
@@ -634,3 +667,9 @@ template void launch_ts_update<double2>(const double2*, int, const double2*, dou
                                         int64_t, cudaStream_t);
 template void launch_ts_trsm<float2>(float2*, int, int64_t, const double2*, cudaStream_t);
 template void launch_ts_trsm<double2>(double2*, int, int64_t, const double2*, cudaStream_t);
+
+void launch_chol_small(const double2* G, int s, double2* R, double* ok, cudaStream_t st) {
+    if (s < 1 || s > 16) throw MbsError{MBS_ERR_ARG, "launch_chol_small: 1 <= s <= 16"};
+    chol_small_kernel<<<1, 32, 0, st>>>(G, s, R, ok);
+    MBS_CHECK_LAUNCH();
+}

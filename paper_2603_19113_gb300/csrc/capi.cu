@@ -91,6 +91,10 @@ struct mbs_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev32, ev64;
 
+    // pinned host staging for the per-step readback of block GMRES
+    double2* pinned = nullptr;
+    size_t pinned_n = 0;
+
     // allocations
     std::vector<void*> geom_allocs;  // freed on rebuild
     std::unordered_map<std::string, DevBuf> bufs;
@@ -691,18 +695,11 @@ GmresStats gmres(mbs_ctx* c, int nrhs, const V* b, V* x, bool x_zero, double tol
 // s*j directions).  Block classical Gram-Schmidt applied twice with the
 // tall-skinny kernels of blas.cu (fixed reduction order, so a solve is bitwise
 // reproducible next to other work); the new block is orthonormalised by CholQR2
-// (Gram matrix and Cholesky on the host in FP64, triangular solve on the
-// device); the block upper Hessenberg least-squares problem is reduced by
-// Givens rotations on the host in FP64.
+// (Gram matrix, FP64 Cholesky and triangular solve, all on the device); each
+// step ends with one readback of the coefficients, and the block upper
+// Hessenberg least-squares problem is reduced by Givens rotations on the host
+// in FP64.
 // ---------------------------------------------------------------------------
-template <typename V>
-void to_host_cd(const V* d, size_t n, std::vector<cd>& out, cudaStream_t st) {
-    std::vector<V> h(n);
-    MBS_CUDA_TRY(cudaMemcpyAsync(h.data(), d, n * sizeof(V), cudaMemcpyDeviceToHost, st));
-    MBS_CUDA_TRY(cudaStreamSynchronize(st));
-    out.resize(n);
-    for (size_t i = 0; i < n; ++i) out[i] = cd((double)h[i].x, (double)h[i].y);
-}
 template <typename V>
 void from_host_cd(const std::vector<cd>& in, V* d, cudaStream_t st, std::vector<V>& stage) {
     stage.resize(in.size());
@@ -713,53 +710,49 @@ void from_host_cd(const std::vector<cd>& in, V* d, cudaStream_t st, std::vector<
     MBS_CUDA_TRY(cudaMemcpyAsync(d, stage.data(), in.size() * sizeof(V), cudaMemcpyHostToDevice, st));
 }
 
-// Cholesky of an s x s Hermitian matrix (column-major): G = R^H R, R upper.
-// Returns false if G is not numerically positive definite.
-bool chol_upper(const std::vector<cd>& G, int s, std::vector<cd>& R) {
-    R.assign((size_t)s * s, cd(0.0));
-    double gmax = 0.0;
-    for (int i = 0; i < s; ++i) gmax = std::max(gmax, G[(size_t)i * s + i].real());
-    for (int j = 0; j < s; ++j) {
-        for (int i = 0; i <= j; ++i) {
-            cd sum = G[(size_t)j * s + i];  // G(i, j)
-            for (int k = 0; k < i; ++k) sum -= std::conj(R[(size_t)i * s + k]) * R[(size_t)j * s + k];
-            if (i == j) {
-                if (!(sum.real() > 1e-13 * gmax)) return false;
-                R[(size_t)j * s + j] = std::sqrt(sum.real());
-            } else {
-                R[(size_t)j * s + i] = sum / R[(size_t)i * s + i].real();
-            }
-        }
+// W (N x s, [s][N]) = Q R with Q orthonormal: two Cholesky-QR passes, all on
+// the device (Gram product, s x s Cholesky, triangular solve), queued without
+// a host synchronisation.  The factors land in Bs: R1 at [0, s^2), R2 at
+// [s^2, 2 s^2), and the two positive-definiteness flags in the next double2.
+template <typename V>
+void cholqr2_dev(mbs_ctx* c, V* W, int64_t N, int s, double2* Bs, double2* d_gram, double2* d_part) {
+    const int nb = ts_gram_blocks(N, s, s);
+    double* ok = reinterpret_cast<double*>(Bs + 2 * s * s);
+    for (int pass = 0; pass < 2; ++pass) {
+        double2* R = Bs + (size_t)pass * s * s;
+        launch_ts_gram<V>(W, s, W, s, N, d_gram, d_part, nb, c->st);
+        launch_chol_small(d_gram, s, R, ok + pass, c->st);
+        launch_ts_trsm<V>(W, s, N, R, c->st);
     }
-    return true;
 }
 
-// W (N x s, [s][N]) = Q R with Q orthonormal: two Cholesky-QR passes.
-// Returns false on (numerical) rank deficiency.
-template <typename V>
-bool cholqr2(mbs_ctx* c, V* W, int64_t N, int s, double2* d_small, double2* d_part,
-             std::vector<cd>& R) {
-    std::vector<cd> G, R1, R2;
-    std::vector<double2> stage;
-    const int nb = ts_gram_blocks(N, s, s);
-    for (int pass = 0; pass < 2; ++pass) {
-        launch_ts_gram<V>(W, s, W, s, N, d_small, d_part, nb, c->st);
-        to_host_cd(d_small, (size_t)s * s, G, c->st);
-        std::vector<cd>& Rp = pass == 0 ? R1 : R2;
-        if (!chol_upper(G, s, Rp)) return false;
-        from_host_cd(Rp, d_small, c->st, stage);
-        launch_ts_trsm<V>(W, s, N, d_small, c->st);
-        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
-    }
-    // R = R2 R1
+// Host side of cholqr2_dev after the readback: R = R2 R1, false if either
+// pass was not positive definite (rank deficiency).
+bool cholqr2_host(const double2* Bs, int s, std::vector<cd>& R) {
+    const double* ok = reinterpret_cast<const double*>(Bs + 2 * s * s);
+    if (!(ok[0] > 0.5 && ok[1] > 0.5)) return false;
+    const double2* R1 = Bs;
+    const double2* R2 = Bs + s * s;
     R.assign((size_t)s * s, cd(0.0));
     for (int j = 0; j < s; ++j)
         for (int i = 0; i <= j; ++i) {
             cd sum = 0.0;
-            for (int k = i; k <= j; ++k) sum += R2[(size_t)k * s + i] * R1[(size_t)j * s + k];
+            for (int k = i; k <= j; ++k)
+                sum += cd(R2[k * s + i].x, R2[k * s + i].y) * cd(R1[j * s + k].x, R1[j * s + k].y);
             R[(size_t)j * s + i] = sum;
         }
     return true;
+}
+
+double2* pinned_stage(mbs_ctx* c, size_t count) {
+    if (c->pinned_n < count) {
+        if (c->pinned) cudaFreeHost(c->pinned);
+        c->pinned = nullptr;
+        c->pinned_n = 0;
+        MBS_CUDA_TRY(cudaMallocHost(&c->pinned, count * sizeof(double2)));
+        c->pinned_n = count;
+    }
+    return c->pinned;
 }
 
 template <typename V>
@@ -773,8 +766,12 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
     V* basis = scratch<V>(c, "bg_basis" + sfx, (size_t)(restart + 1) * NV);
     V* w = scratch<V>(c, "gm_w" + sfx, NV);
     V* r = scratch<V>(c, "gm_r" + sfx, NV);
-    double2* d_h = scratch<double2>(c, "bg_h", (size_t)(restart + 1) * s * s);
-    double2* d_small = scratch<double2>(c, "bg_small", (size_t)s * s);
+    // per step, read back in one copy: [R1 | R2 | ok | Hcol pass 1 (K s) | Hcol pass 2 (K s)]
+    const size_t sq = (size_t)s * s;
+    const size_t nsmall = 2 * sq + 1 + 2 * (size_t)restart * sq;
+    double2* Bs = scratch<double2>(c, "bg_small", nsmall);
+    double2* d_gram = scratch<double2>(c, "bg_gram", sq);
+    double2* hb = pinned_stage(c, nsmall);
     // partial sums of the Gram products (nblk * ka * s for every block width ka used)
     size_t part = 0;
     for (int j = 0; j < restart; ++j) {
@@ -819,7 +816,10 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         MBS_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), s * sizeof(double), cudaMemcpyHostToDevice, c->st));
         launch_scale<V>(r, d_inv, basis, N, s, c->st);
         std::vector<cd> Rq;
-        if (!cholqr2<V>(c, basis, N, s, d_small, d_part, Rq)) break;  // R0 numerically rank deficient
+        cholqr2_dev<V>(c, basis, N, s, Bs, d_gram, d_part);
+        MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1) * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+        MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+        if (!cholqr2_host(hb, s, Rq)) break;  // R0 numerically rank deficient
         H.assign((size_t)ldH * M, cd(0.0));
         G.assign((size_t)ldH * s, cd(0.0));  // right-hand side of the small LS, column-major ldH
         for (int q = 0; q < s; ++q)
@@ -833,20 +833,29 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             apply_op<V>(c, s, vj, w);
             S.matvecs++;
             const int K = (j + 1) * s;
-            // block CGS2: Hcol = V^H W; W -= V Hcol (twice)
-            Hcol.assign((size_t)K * s, cd(0.0));
+            // block CGS2: Hcol = V^H W; W -= V Hcol (twice), then CholQR2 of the new
+            // block; one readback of both coefficient blocks and both factors
+            double2* h1 = Bs + 2 * sq + 1;
+            double2* h2 = h1 + (size_t)K * s;
             for (int pass = 0; pass < 2; ++pass) {
-                launch_ts_gram<V>(basis, K, w, s, N, d_h, d_part, ts_gram_blocks(N, K, s), c->st);
-                launch_ts_update<V>(basis, K, d_h, -1.0, w, s, N, c->st);
-                std::vector<cd> hp;
-                to_host_cd(d_h, (size_t)K * s, hp, c->st);
-                for (size_t e = 0; e < hp.size(); ++e) Hcol[e] += hp[e];
+                double2* hp = pass == 0 ? h1 : h2;
+                launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s), c->st);
+                launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st);
             }
             V* vn = basis + (size_t)(j + 1) * NV;
             MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
-            if (!cholqr2<V>(c, vn, N, s, d_small, d_part, Rk)) {
+            cholqr2_dev<V>(c, vn, N, s, Bs, d_gram, d_part);
+            MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1 + 2 * (size_t)K * s) * sizeof(double2),
+                                         cudaMemcpyDeviceToHost, c->st));
+            MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+            Hcol.assign((size_t)K * s, cd(0.0));
+            for (size_t e = 0; e < (size_t)K * s; ++e) {
+                const double2 a1 = hb[2 * sq + 1 + e], a2 = hb[2 * sq + 1 + (size_t)K * s + e];
+                Hcol[e] = cd(a1.x + a2.x, a1.y + a2.y);
+            }
+            if (!cholqr2_host(hb, s, Rk)) {
                 breakdown = true;  // the new block adds no direction: the solution is in the space
-                Rk.assign((size_t)s * s, cd(0.0));
+                Rk.assign(sq, cd(0.0));
             }
             S.iters++;
             jdone = j + 1;
@@ -1436,6 +1445,8 @@ void mbs_destroy(mbs_ctx* c) {
         c->bufs.clear();
         dfree(c, c->d_err);
         c->d_err = nullptr;
+        if (c->pinned) cudaFreeHost(c->pinned);
+        c->pinned = nullptr;
         if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     }
     delete c;

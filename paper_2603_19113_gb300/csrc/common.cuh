@@ -157,6 +157,9 @@ void launch_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t st);
 // (R upper triangular, FP64).  ts_gram needs scratch of nblk * ka * kb
 // double2 with nblk = ts_gram_blocks(N, ka, kb); kb <= 16 for update/trsm.
 int ts_gram_blocks(int64_t N, int ka, int kb);
+// Cholesky G = R^H R of an s x s Hermitian matrix on the device (s <= 16);
+// *ok = 1, or 0 (and R = I) if G is not numerically positive definite.
+void launch_chol_small(const double2* G, int s, double2* R, double* ok, cudaStream_t st);
 template <typename V>
 void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* C,
                     double2* scratch, int nblk, cudaStream_t st);
