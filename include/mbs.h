@@ -80,6 +80,8 @@ typedef struct mbs_options {
     int autotune;        /* 1 (default): the first FP32 G_hat matvec of a problem class times the candidate
                             launch shapes (kernel path x source-split count) and the fastest is reused process-wide;
                             0: heuristic shape */
+    int cuda_graphs;     /* 1 (default): after one direct step, the device work of each block-GMRES step is
+                            captured once per context and step index and replayed as a CUDA graph; 0: launch directly */
 } mbs_options;
 
 typedef struct mbs_shape {
@@ -114,7 +116,7 @@ typedef struct mbs_ctx mbs_ctx;
 
 /* Fill *opt with defaults: FP64, tol 1e-11, inner_tol 1e-6, restart 60,
  * max_iter 20000, max_sweeps 8, ls_rcond 1e-14, stream NULL, no budget,
- * automatic G_hat kernel, autotuning on. */
+ * automatic G_hat kernel, autotuning and CUDA graphs on. */
 void mbs_default_options(mbs_options* opt);
 
 /* Create a context for dimension dim (2 or 3) and wavenumber kappa > 0

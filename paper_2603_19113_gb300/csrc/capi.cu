@@ -43,6 +43,15 @@ struct ShapeHost {
     int* permA = nullptr;
 };
 
+// One captured block-GMRES step (operator, block Gram-Schmidt, CholQR2 and the
+// readback), replayed by cudaGraphLaunch.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;  // G_hat timing inside the graph (profiling)
+    int prec = 0;                             // 0: FP32 G_hat, 1: FP64
+    long long launches = 0;                   // library kernels in the graph
+};
+
 }  // namespace
 
 struct mbs_ctx {
@@ -95,6 +104,15 @@ struct mbs_ctx {
     double2* pinned = nullptr;
     size_t pinned_n = 0;
 
+    // CUDA graphs of block-GMRES steps, keyed by (vector type, s, step, restart,
+    // buffer addresses); dropped whenever a buffer they use may move
+    std::map<std::array<int64_t, 8>, StepGraph> graphs;
+    bool capturing = false;
+    bool graphs_off = false;  // a capture failed on this context: run steps directly
+    cudaEvent_t cap_e0 = nullptr, cap_e1 = nullptr;
+    double graph_ms[2] = {0.0, 0.0};  // profiled G_hat time of replayed steps (FP32, FP64)
+    long long graph_n[2] = {0, 0};
+
     // allocations
     std::vector<void*> geom_allocs;  // freed on rebuild
     std::unordered_map<std::string, DevBuf> bufs;
@@ -138,11 +156,24 @@ T* galloc(mbs_ctx* c, size_t count) {
     return p;
 }
 
+void clear_graphs(mbs_ctx* c) {
+    if (c->graphs.empty()) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.e0) cudaEventDestroy(kv.second.e0);
+        if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+    }
+    c->graphs.clear();
+}
+
 template <typename T>
 T* scratch(mbs_ctx* c, const std::string& name, size_t count) {
     DevBuf& b = c->bufs[name];
     const size_t need = count * sizeof(T);
     if (b.n < need) {
+        if (c->capturing) throw MbsError{MBS_ERR_STATE, "buffer growth inside a graph capture"};
+        clear_graphs(c);  // captured steps may refer to the old buffer
         if (b.p) {
             MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
             dfree(c, b.p);
@@ -156,6 +187,7 @@ T* scratch(mbs_ctx* c, const std::string& name, size_t count) {
 }
 
 void free_geometry(mbs_ctx* c) {
+    clear_graphs(c);
     if (c->st) cudaStreamSynchronize(c->st);
     for (void* p : c->geom_allocs) dfree(c, p);
     c->geom_allocs.clear();
@@ -430,7 +462,10 @@ Shape32 shape32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
 void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
     const Shape32 sh = shape32(c, nrhs, x, y);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->profile) {
+    if (c->profile && c->capturing) {
+        e0 = c->cap_e0;  // recorded on every replay of the step graph
+        e1 = c->cap_e1;
+    } else if (c->profile) {
         e0 = take_event(c);
         e1 = take_event(c);
         c->ev32.emplace_back(e0, e1);
@@ -442,7 +477,10 @@ void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
     int* sb = split_for(c, c->N, &ns);
     double2* part = scratch<double2>(c, "part64", (size_t)ns * nrhs * c->N);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->profile) {
+    if (c->profile && c->capturing) {
+        e0 = c->cap_e0;
+        e1 = c->cap_e1;
+    } else if (c->profile) {
         e0 = take_event(c);
         e1 = take_event(c);
         c->ev64.emplace_back(e0, e1);
@@ -755,6 +793,56 @@ double2* pinned_stage(mbs_ctx* c, size_t count) {
     return c->pinned;
 }
 
+// Run one block-GMRES step from its CUDA graph, capturing it at first use.
+// Returns the graph (for its profiling events), or nullptr if the step could
+// not be captured; the caller then enqueues the step directly.
+template <typename F>
+StepGraph* run_step_graph(mbs_ctx* c, const std::array<int64_t, 8>& key, int prec, F&& enqueue) {
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        StepGraph g;
+        g.prec = prec;
+        if (c->profile) {
+            MBS_CUDA_TRY(cudaEventCreate(&g.e0));
+            MBS_CUDA_TRY(cudaEventCreate(&g.e1));
+        }
+        auto fail = [&]() -> StepGraph* {
+            cudaGetLastError();
+            if (g.e0) cudaEventDestroy(g.e0);
+            if (g.e1) cudaEventDestroy(g.e1);
+            c->graphs_off = true;
+            return nullptr;
+        };
+        if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail();
+        c->capturing = true;
+        c->cap_e0 = g.e0;
+        c->cap_e1 = g.e1;
+        const long long l0 = g_mbs_launches.load();
+        bool ok = true;
+        try {
+            enqueue();
+        } catch (const MbsError&) {
+            ok = false;
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->st, &graph);
+        c->capturing = false;
+        g.launches = g_mbs_launches.load() - l0;
+        g_mbs_launches.fetch_sub(g.launches);  // nothing ran during the capture
+        if (!ok || ee != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail();
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return fail();
+        it = c->graphs.emplace(key, g).first;
+    }
+    MBS_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->st));
+    g_mbs_launches.fetch_add(it->second.launches);
+    return &it->second;
+}
+
 template <typename V>
 GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, int restart,
                   int maxit, bool verify) {
@@ -793,6 +881,7 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
     const int ldH = (restart + 1) * s;  // its rows
     std::vector<cd> H, G, Hcol, Rk, cs_, sn_;
     double prev_worst = 1e300;
+    bool warm = false;
     while (true) {
         const std::vector<double> beta = norms<V>(c, r, s);
         double worst = 0.0;
@@ -829,25 +918,45 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         int jdone = 0;
         bool breakdown = false;
         for (int j = 0; j < restart && S.iters < maxit; ++j) {
-            V* vj = basis + (size_t)j * NV;
-            apply_op<V>(c, s, vj, w);
-            S.matvecs++;
             const int K = (j + 1) * s;
-            // block CGS2: Hcol = V^H W; W -= V Hcol (twice), then CholQR2 of the new
-            // block; one readback of both coefficient blocks and both factors
-            double2* h1 = Bs + 2 * sq + 1;
-            double2* h2 = h1 + (size_t)K * s;
-            for (int pass = 0; pass < 2; ++pass) {
-                double2* hp = pass == 0 ? h1 : h2;
-                launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s), c->st);
-                launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st);
+            // the step's device work, queued without host synchronisation: operator,
+            // block CGS2 (Hcol = V^H W; W -= V Hcol, twice), CholQR2 of the new block
+            // and one readback of both coefficient blocks and both factors
+            auto enqueue = [&]() {
+                V* vj = basis + (size_t)j * NV;
+                apply_op<V>(c, s, vj, w);
+                double2* h1 = Bs + 2 * sq + 1;
+                double2* h2 = h1 + (size_t)K * s;
+                for (int pass = 0; pass < 2; ++pass) {
+                    double2* hp = pass == 0 ? h1 : h2;
+                    launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s), c->st);
+                    launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st);
+                }
+                V* vn = basis + (size_t)(j + 1) * NV;
+                MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
+                cholqr2_dev<V>(c, vn, N, s, Bs, d_gram, d_part);
+                MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1 + 2 * (size_t)K * s) * sizeof(double2),
+                                             cudaMemcpyDeviceToHost, c->st));
+            };
+            // after one direct step (autotuning, buffer allocation) the steps run
+            // from CUDA graphs captured once per context and step index
+            StepGraph* sg = nullptr;
+            if (warm && c->opt.cuda_graphs && !c->graphs_off) {
+                const std::array<int64_t, 8> key{(int64_t)sizeof(V), s, j, restart, (int64_t)(intptr_t)basis,
+                                                 (int64_t)(intptr_t)w, (int64_t)(intptr_t)Bs,
+                                                 (int64_t)(intptr_t)hb};
+                sg = run_step_graph(c, key, sizeof(V) == 8 ? 0 : 1, enqueue);
             }
-            V* vn = basis + (size_t)(j + 1) * NV;
-            MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
-            cholqr2_dev<V>(c, vn, N, s, Bs, d_gram, d_part);
-            MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1 + 2 * (size_t)K * s) * sizeof(double2),
-                                         cudaMemcpyDeviceToHost, c->st));
+            if (!sg) enqueue();
+            S.matvecs++;
             MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+            warm = true;
+            if (sg && sg->e0) {
+                float ms = 0.f;
+                MBS_CUDA_TRY(cudaEventElapsedTime(&ms, sg->e0, sg->e1));
+                c->graph_ms[sg->prec] += ms;
+                c->graph_n[sg->prec] += 1;
+            }
             Hcol.assign((size_t)K * s, cd(0.0));
             for (size_t e = 0; e < (size_t)K * s; ++e) {
                 const double2 a1 = hb[2 * sq + 1 + e], a2 = hb[2 * sq + 1 + (size_t)K * s + e];
@@ -1064,6 +1173,7 @@ void check_geometry(mbs_ctx* c) {
 
 // Skeleton layout, body-pair table, S pointer tables, right-hand-side descriptors.
 void setup_layout(mbs_ctx* c) {
+    clear_graphs(c);  // captured steps refer to the layout's tables
     const int T = c->T, d = c->dim;
     c->off.assign(T + 1, 0);
     c->voff.assign(T + 1, 0);
@@ -1358,6 +1468,7 @@ void mbs_default_options(mbs_options* o) {
     o->block_krylov = 1;
     o->mac_path = 0;
     o->autotune = 1;
+    o->cuda_graphs = 1;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {
@@ -1396,6 +1507,7 @@ int64_t mbs_launch_count(void) { return (int64_t)g_mbs_launches.load(); }
 
 mbs_status mbs_profile(mbs_ctx* c, int enable) {
     return guarded(c, [&]() {
+        if ((enable != 0) != c->profile) clear_graphs(c);  // graphs hold timing events or not
         c->profile = enable != 0;
         return MBS_OK;
     });
@@ -1418,10 +1530,12 @@ mbs_status mbs_kernel_times(mbs_ctx* c, double* out) {
             }
             lists[a]->clear();
         }
-        out[0] = t[0];
-        out[1] = (double)n[0];
-        out[2] = t[1];
-        out[3] = (double)n[1];
+        out[0] = t[0] + c->graph_ms[0];
+        out[1] = (double)n[0] + (double)c->graph_n[0];
+        out[2] = t[1] + c->graph_ms[1];
+        out[3] = (double)n[1] + (double)c->graph_n[1];
+        c->graph_ms[0] = c->graph_ms[1] = 0.0;
+        c->graph_n[0] = c->graph_n[1] = 0;
         return MBS_OK;
     });
 }
@@ -1465,6 +1579,7 @@ mbs_status mbs_set_options(mbs_ctx* c, const mbs_options* opt) {
             c->st = (cudaStream_t)opt->stream;
         }
         void* keep = c->opt.stream;
+        clear_graphs(c);
         c->opt = *opt;
         if (!opt->stream) c->opt.stream = keep;
         return MBS_OK;

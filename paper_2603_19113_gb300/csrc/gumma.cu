@@ -566,8 +566,16 @@ void launch_umma_block(const GLayout& L, const F32Const& K, const UmmaLayout& U,
     g_umma_pack_kernel<DIM, NR><<<(unsigned)U.nchunks, 128, 0, st>>>(L, nrhs, r0, q, U.chunk_off,
                                                                      U.chunk_body, U.pack);
     MBS_CHECK_LAUNCH();
-    MBS_CUDA_TRY(cudaFuncSetAttribute(g_umma_kernel<DIM, NR>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM));
+    // once per device (keeps the call out of captured CUDA graphs)
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    MBS_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        MBS_CUDA_TRY(cudaFuncSetAttribute(g_umma_kernel<DIM, NR>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, UM_SMEM));
+        attr_set.fetch_or(bit);
+    }
     dim3 grid((unsigned)((L.N + UM_T - 1) / UM_T), (unsigned)nsplit);
     g_umma_kernel<DIM, NR><<<grid, UM_THREADS, UM_SMEM, st>>>(L, K, nrhs, r0, U.pack, U.chunk_off, part,
                                                         sb, U.err);

@@ -196,6 +196,24 @@ def test_injected_solve_fp64_and_mixed_config0(pkg):
         assert _rel(u, u_ref) < tol
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_block_gmres_graph_replay_matches_direct(pkg, prec):
+    """Block GMRES steps replayed from captured CUDA graphs give bitwise the
+    result of the same steps launched directly (short restart, so step graphs
+    are reused across restart cycles and refinement sweeps)."""
+    wl = mi.tiny_2d(seed=3, T=9, kappa=6.0, nrhs=3)
+    p = pkg.PREC_MIXED if prec == "mixed" else pkg.PREC_FP64
+    out = []
+    for graphs in (1, 0):
+        ctx = pkg.Context(2, wl.kappa, precision=p, tol=1e-10, restart=4, cuda_graphs=graphs)
+        ctx.build_scattering_matrices(wl)
+        q, info = ctx.solve(ctx.rhs(wl.boundary_data()))
+        assert info["converged"] == 1 and info["inner_iterations"] > 8
+        out.append(q)
+        ctx.close()
+    assert np.array_equal(out[0], out[1])
+
+
 def test_evaluate_field_matches_oracle(pkg):
     wl = mi.tiny_2d(seed=3, T=7, kappa=5.0)
     ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
