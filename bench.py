@@ -37,6 +37,9 @@ WORKLOAD = ("2D sound-soft, 1000 bodies (circle, 3-star, ellipse 1:0.6; radius 1
             "per body (N=64,000), 8 plane waves; mixed FP32/FP64-IR solve to rel. residual 1e-11")
 FLOPS_PER_PAIR_2D = lambda nrhs: 35 + 8 * nrhs  # noqa: E731  (convention)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+# DRAM bytes (read + write) of one launch on this workload, from one ncu capture
+# (profiles/g_umma_kernel_2d_1000bodies_8rhs.md); null for kernels not captured
+TRAFFIC_BYTES = {"g_umma_kernel<2,8>": 34230016 + 138496}
 
 
 def parse():
@@ -94,7 +97,18 @@ def run_serving(a, pkg, mi):
     first = min(srv.poll(rid)["t_submit"] for _, rid in ids)
     srv.close()
     lat = np.array(lat)
+    waits, serv = [], []
+    for r, rid in ids:
+        res = srv.poll(rid)
+        if res["done"] == 1:
+            waits.append(res["t_start"] - res["t_submit"])
+            serv.append(res["t_end"] - res["t_start"])
+            print(f"served: rid={r.rid} dim={r.dim} T={r.T} N={res['N']} nrhs={r.nrhs} kappa={r.kappa:.1f} "
+                  f"iterations={res['inner_iterations']} wait_s={waits[-1]:.2f} service_s={serv[-1]:.2f}",
+                  file=sys.stderr)
     return {"requests": len(ids), "failed": fails,
+            "mean_wait_s": float(np.mean(waits)) if waits else None,
+            "mean_service_s": float(np.mean(serv)) if serv else None,
             "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "solves_per_s": len(done) / (max(done) - first) if done else None,
@@ -453,10 +467,12 @@ def run_mbs(a, ws, rank, local):
     flops_launch = pairs_mv * FLOPS_PER_PAIR_2D(nrhs)
     avg_ms = kt["g32_ms"] / max(1, kt["g32_launches"])
     achieved = flops_launch / (avg_ms / 1e3) / 1e12
-    kname = {1: "g_f32_kernel<2,8,2>", 2: "g_tc_kernel<2,1>"}.get(a.mac, "g_umma_kernel<2,8>")
+    kname = {1: "g_f32_kernel<2,8,2>", 2: "g_tc_kernel<2,1>", 3: "g_umma_kernel<2,8>"}.get(
+        kt["g32_path"], "unknown")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None, "avg_launch_ms": avg_ms, "launches": kt["g32_launches"],
+                "traffic": TRAFFIC_BYTES.get(kname), "avg_launch_ms": avg_ms,
+                "launches": kt["g32_launches"], "nsplit": kt["g32_nsplit"],
                 "flops_per_launch": flops_launch,
                 "peak_note": "FP32 SIMT peak from unit counts: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     share = kt["g32_ms"] / ms if ms > 0 else None

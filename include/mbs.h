@@ -248,7 +248,9 @@ mbs_status mbs_profile(mbs_ctx* ctx, int enable);
 
 /* Sum the bracketed G_hat kernel times since the last call and reset:
  * out[0] = total ms of FP32 G_hat launches, out[1] = their count,
- * out[2] = total ms of FP64 G_hat launches, out[3] = their count.
+ * out[2] = total ms of FP64 G_hat launches, out[3] = their count,
+ * out[4] = kernel path of the latest FP32 G_hat (mac_path numbering; 0 if
+ * none), out[5] = its source-split count.  out must hold 6 doubles.
  * Synchronises the context's stream. */
 mbs_status mbs_kernel_times(mbs_ctx* ctx, double* out);
 

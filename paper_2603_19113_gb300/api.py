@@ -308,10 +308,10 @@ def _ctx_profile(self, enable: bool = True):
 
 
 def _ctx_kernel_times(self) -> dict:
-    out = (C.c_double * 4)()
+    out = (C.c_double * 6)()
     self._check(_lib().mbs_kernel_times(self._h, out))
     return {"g32_ms": out[0], "g32_launches": int(out[1]), "g64_ms": out[2],
-            "g64_launches": int(out[3])}
+            "g64_launches": int(out[3]), "g32_path": int(out[4]), "g32_nsplit": int(out[5])}
 
 
 Context.profile = _ctx_profile

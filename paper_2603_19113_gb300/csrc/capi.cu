@@ -111,6 +111,7 @@ struct mbs_ctx {
     bool graphs_off = false;  // a capture failed on this context: run steps directly
     cudaEvent_t cap_e0 = nullptr, cap_e1 = nullptr;
     double graph_ms[2] = {0.0, 0.0};  // profiled G_hat time of replayed steps (FP32, FP64)
+    int last_path = 0, last_nsplit = 0;  // launch shape of the latest FP32 G_hat
     long long graph_n[2] = {0, 0};
 
     // allocations
@@ -471,6 +472,8 @@ void G32(mbs_ctx* c, int nrhs, const float2* x, float2* y) {
         c->ev32.emplace_back(e0, e1);
     }
     launch_g32(c, nrhs, x, y, sh, e0, e1);
+    c->last_path = sh.path;
+    c->last_nsplit = sh.nsplit;
 }
 void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
     int ns;
@@ -1534,6 +1537,8 @@ mbs_status mbs_kernel_times(mbs_ctx* c, double* out) {
         out[1] = (double)n[0] + (double)c->graph_n[0];
         out[2] = t[1] + c->graph_ms[1];
         out[3] = (double)n[1] + (double)c->graph_n[1];
+        out[4] = c->last_path;
+        out[5] = c->last_nsplit;
         c->graph_ms[0] = c->graph_ms[1] = 0.0;
         c->graph_n[0] = c->graph_n[1] = 0;
         return MBS_OK;
