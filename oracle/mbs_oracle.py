@@ -18,6 +18,11 @@ What it follows, step by step, in the paper's order and notation:
   solve_dense    (I + S G_hat) q_hat = b by LU                 (Sec. 2.2)
   gmres          unrestarted GMRES, MGS Arnoldi + Givens       (Sec. 2.4; Saad & Schultz 1986)
   field          u(x) = sum_i phi(x - x_hat_i) q_hat_i          (Sec. 4.1, eq. out_skel)
+  reconstruct_mfs  q_mfs_tau = A^+ (v_tau - U_tau G_hat_{tau,tau^c} q_hat_{tau^c})
+                                                               (Sec. 4.6, MFS-surface reconstruction)
+  field_near     u(x) anywhere outside the MFS curves: skeleton sums of the bodies
+                 whose proxy surface x lies outside, MFS sums of the one it lies in
+                                                               (Sec. 4.6)
 
 Readings where the paper is silent (each listed in the design doc):
   * pivot rule: largest remaining column norm, recomputed in full at every
@@ -30,7 +35,10 @@ Readings where the paper is silent (each listed in the design doc):
 Pins (tests, -m "not gpu"): separation-of-variables closed forms for a circle
 (2D) and a sphere (3D), reciprocity, dense LU vs GMRES, a brute-force global
 MFS on tiny inputs, the ID identities, rigid-motion invariance, and textbook
-values of H0.  No function here is "parity unpinned".
+values of H0; for the reconstruction, the circle series between Gamma and the
+proxy, the sound-soft condition on Gamma between collocation points (and its
+spectral decay), and agreement of MFS and skeleton sources away from a body.
+No function here is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -43,7 +51,8 @@ from scipy.special import hankel1
 __all__ = [
     "phi", "kernel_matrix", "cpqr_id", "tsvd_solve", "tsvd_pinv", "build_shape", "build_all",
     "layout", "apply_W", "G_dense", "G_matvec", "G_rows", "apply_operator", "rhs", "solve_dense", "gmres",
-    "field", "solve_workload", "incoming_on_boundary",
+    "field", "solve_workload", "incoming_on_boundary", "reconstruct_mfs", "field_near",
+    "proxy_body",
 ]
 
 TIE_TOL = 1e-10
@@ -370,6 +379,61 @@ def incoming_on_boundary(wl, sdata, lay, qhat, v) -> np.ndarray:
         out.append(v[off:off + m] - K @ q2)
         off += m
     return np.concatenate(out, axis=0)
+
+
+def reconstruct_mfs(wl, sdata, lay, qhat, v) -> list:
+    """Full local solution on the MFS curve/surface of every body (Sec. 4.6):
+    q_mfs_tau = A_tau^+ (v_tau - U_tau G_hat_{tau,tau^c} q_hat_{tau^c}), where
+    G_hat_{tau,tau^c} q_hat_{tau^c} is the incoming field at tau's skeleton points
+    from every other body and U_tau = (Z*_tau)^T interpolates it to all m
+    collocation points (Sec. 4.3, eq. inc_field).  A^+ is the truncated-SVD
+    solve.  Returns one (n_tau, nrhs) array per body."""
+    xhat, body = lay["xhat"], lay["body"]
+    q2 = qhat.reshape(xhat.shape[0], -1)
+    v2 = v.reshape(v.shape[0], -1)
+    w_hat = G_matvec(wl.dim, wl.kappa, xhat, body, q2)
+    out, voff = [], 0
+    for t in range(wl.T):
+        sd = sdata[int(wl.body_shape[t])]
+        a, b = lay["offsets"][t], lay["offsets"][t + 1]
+        m = sd["Zs"].shape[1]
+        resid = v2[voff:voff + m] - sd["Zs"].T @ w_hat[a:b]
+        Ua, sa, Vh = sd["A_svd"]
+        out.append(Vh.conj().T @ ((Ua.conj().T @ resid) / sa[:, None]))
+        voff += m
+    return out
+
+
+def proxy_body(wl, targets) -> np.ndarray:
+    """Index of the body whose proxy surface strictly contains each target, or -1."""
+    d = wl.dim
+    tb = np.full(targets.shape[0], -1, dtype=np.int64)
+    rp = wl.proxy_radius_of_body()
+    for t in range(wl.T):
+        inside = np.sum((targets - wl.centres[t, :d]) ** 2, axis=1) < rp[t] ** 2 * (1.0 - 1e-12)
+        tb[inside] = t
+    return tb
+
+
+def field_near(wl, sdata, lay, qhat, qmfs, targets) -> np.ndarray:
+    """Scattered field at targets anywhere outside the MFS curves (Sec. 4.6): a
+    target inside the proxy surface of body tau gets the MFS sum of tau plus the
+    skeleton sums (eq. out_skel) of every other body; any other target gets the
+    skeleton sums of all bodies."""
+    d = wl.dim
+    xhat, body = lay["xhat"], lay["body"]
+    q2 = qhat.reshape(xhat.shape[0], -1)
+    tb = proxy_body(wl, targets)
+    out = np.zeros((targets.shape[0], q2.shape[1]), dtype=np.complex128)
+    for i in range(targets.shape[0]):
+        x = targets[i:i + 1]
+        t = tb[i]
+        keep = body != t
+        out[i] = (kernel_matrix(d, wl.kappa, x, xhat[keep]) @ q2[keep])[0]
+        if t >= 0:
+            qm = qmfs[t].reshape(qmfs[t].shape[0], -1)
+            out[i] += (kernel_matrix(d, wl.kappa, x, wl.body_points(int(t), "y")) @ qm)[0]
+    return out
 
 
 def solve_workload(wl, method: str = "auto", tol: float = 1e-13):

@@ -289,3 +289,75 @@ def test_starfish_skeleton_counts_loose():
         prev = ks[0]
         if kappa == 25.0:
             assert abs(ks[0] - nskel) <= 0.15 * nskel
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.6: reconstruction on the MFS curve and the field near a body
+# --------------------------------------------------------------------------
+def _boundary_midpoints(wl, t):
+    """Points on Gamma_tau halfway (in the curve parameter) between collocation
+    points: the sound-soft condition u + u_inc = 0 holds there only through the
+    solve, not by construction."""
+    from mbs_inputs.workloads import _curve
+    sh = wl.shapes[int(wl.body_shape[t])]
+    th = 2 * np.pi * (np.arange(sh.m) + 0.5) / sh.m
+    return wl.centres[t, :2] + _curve(sh.name, th, 1.0) @ wl.rots[t, :2, :2].T
+
+
+def _circles_and_stars(m, kinds):
+    wl = mi.tiny_2d(seed=0, T=4, kappa=6.0, nrhs=2, ks=(0, 0, 0), eps=1e-12)
+    for i, kind in enumerate(kinds):
+        wl.shapes[i] = mi.shape_2d(kind, m, m // 2, m + 1, 1.3, k=0, eps=1e-12)
+    return wl
+
+
+def _einc(wl):
+    """max over bodies and boundary midpoints of |u_scat + u_inc| (|u_inc| = 1)."""
+    res = orc.solve_workload(wl)
+    qm = orc.reconstruct_mfs(wl, res["sdata"], res["layout"], res["q"], res["v"])
+    errs = []
+    for t in range(wl.T):
+        X = _boundary_midpoints(wl, t)
+        u = orc.field_near(wl, res["sdata"], res["layout"], res["q"], qm, X)
+        errs.append(np.max(np.abs(u + wl.incident(X))))
+    return max(errs), res, qm
+
+
+@pytest.mark.parametrize("kappa", [1.0, 10.0])
+def test_near_field_circle_closed_form(kappa):
+    """One circle: the reconstructed MFS sources (q_mfs = A^+ v, no coupling)
+    give the series solution between Gamma and the proxy circle."""
+    wl = mi.circle_single(kappa, m=128, eps=1e-12, proxy_factor=2.0)
+    res = orc.solve_workload(wl)
+    qm = orc.reconstruct_mfs(wl, res["sdata"], res["layout"], res["q"], res["v"])
+    th = np.linspace(0.0, 2 * np.pi, 97)[:-1]
+    for R, tol in ((1.3, 1e-11), (1.05, 1e-8)):
+        t = R * np.stack([np.cos(th), np.sin(th)], axis=1)
+        assert np.all(orc.proxy_body(wl, t) == 0)
+        u = orc.field_near(wl, res["sdata"], res["layout"], res["q"], qm, t)[:, 0]
+        assert _relerr(u, circle_scattered(kappa, 1.0, 0.0, t)) < tol
+
+
+def test_near_field_boundary_condition_circles():
+    """Four circular bodies: the total field vanishes on every Gamma_tau
+    between the collocation points (E_inc of Sec. 5.1) to 1e-10, which needs the
+    coupling term U G_hat q_hat of the reconstruction with the right sign and
+    indices; far from a body its MFS sources and its skeleton sources give the
+    same field."""
+    wl = _circles_and_stars(160, ("circle", "circle", "circle"))
+    e, res, qm = _einc(wl)
+    assert e < 1e-10
+    th = np.linspace(0.0, 2 * np.pi, 33)[:-1]
+    P = wl.centres[0, :2] + 1.45 * np.stack([np.cos(th), np.sin(th)], axis=1)
+    sk = res["layout"]["body"] == 0
+    us = orc.kernel_matrix(2, wl.kappa, P, res["layout"]["xhat"][sk]) @ res["q"][sk]
+    um = orc.kernel_matrix(2, wl.kappa, P, wl.body_points(0, "y")) @ qm[0]
+    assert _relerr(um, us) < 1e-10
+
+
+def test_near_field_boundary_condition_converges_for_stars():
+    """With non-convex 3-star bodies the boundary residual decays spectrally
+    with the number of collocation points (Sec. 5.1: E_inc falls with N)."""
+    e96, _, _ = _einc(_circles_and_stars(96, ("star3n", "ellipse", "circle")))
+    e256, _, _ = _einc(_circles_and_stars(256, ("star3n", "ellipse", "circle")))
+    assert e256 < 1e-5 and e256 < 1e-3 * e96
