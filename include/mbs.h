@@ -188,10 +188,34 @@ mbs_status mbs_solve(mbs_ctx* ctx, int nrhs, const double* b, double* qhat, mbs_
  * evaluate_field(points): scattered field u(t) = sum_i phi(t - x_hat_i) q_hat_i
  * (Sec. 4.1, eq. out_skel) at M targets (SoA dim * M), in FP64.  Every target
  * must lie on or outside every proxy surface; otherwise MBS_ERR_NEAR_TARGET
- * (near-field reconstruction, Sec. 4.6, is not provided).  u: M x nrhs.
+ * (for targets inside a proxy use mbs_evaluate_field_near).  u: M x nrhs.
  */
 mbs_status mbs_evaluate_field(mbs_ctx* ctx, int nrhs, int64_t M, const double* pts,
                               const double* qhat, double* u);
+
+/*
+ * Full local solution on the MFS curves (Sec. 4.6, reconstruction on
+ * Gamma^mfs):  q_mfs_tau = A_tau^+ (v_tau - U_tau G_hat_{tau,tau^c} q_hat_{tau^c}),
+ * the incoming field from the other bodies taken at tau's skeleton points and
+ * interpolated to its collocation points by U_tau = (Z*_tau)^T (Sec. 4.3,
+ * eq. inc_field), A^+ the truncated pivoted-QR solve of the build.
+ * v: sum_tau m_tau x nrhs boundary data (as for mbs_rhs); qhat: N x nrhs;
+ * qmfs (out): sum_tau n_tau x nrhs, body tau's n_tau rows in body order.
+ * Needs the built scattering data: MBS_ERR_STATE after mbs_inject_scattering.
+ */
+mbs_status mbs_reconstruct(mbs_ctx* ctx, int nrhs, const double* v, const double* qhat, double* qmfs);
+
+/*
+ * Scattered field at M targets anywhere outside the MFS curves (Sec. 4.6):
+ * a target inside the proxy surface of body tau gets tau's field from its MFS
+ * sources qmfs (mbs_reconstruct) plus the skeleton sums (Sec. 4.1,
+ * eq. out_skel) of all other bodies; any other target gets the skeleton sums
+ * of every body, as in mbs_evaluate_field.  pts: SoA dim x M; u: M x nrhs.
+ * Targets on or inside an MFS curve are the caller's responsibility (the
+ * representation is singular there).
+ */
+mbs_status mbs_evaluate_field_near(mbs_ctx* ctx, int nrhs, int64_t M, const double* pts,
+                                   const double* qhat, const double* qmfs, double* u);
 
 /*
  * Test hook: replace the built scattering data of one shape with externally

@@ -79,6 +79,8 @@ SIGNATURES = {
     "mbs_apply_G": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "mbs_solve": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(mbs_solve_info)]),
     "mbs_evaluate_field": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P]),
+    "mbs_reconstruct": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "mbs_evaluate_field_near": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P]),
     "mbs_inject_scattering": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), _P, _P]),
     "mbs_measure_peaks": (C.c_int, [_D]),
     "mbs_apply_G_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_int64, C.c_int, _P, _P, _P,

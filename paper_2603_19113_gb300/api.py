@@ -175,6 +175,7 @@ class Context:
         self.N = int(N.value)
         self.T = wl.T
         self.Mtot = int(sum(wl.shapes[s].m for s in wl.body_shape))
+        self.Nm = int(sum(wl.shapes[s].n for s in wl.body_shape))
         return self
 
     def get_layout(self):
@@ -253,6 +254,34 @@ class Context:
             M = np.asarray(pts).shape[0]
         out, p = _out_like(a, M)
         self._check(_lib().mbs_evaluate_field(self._h, a.nrhs, M, pp, a.ptr, p))
+        return _ret(out, a)
+
+    def reconstruct(self, v, qhat):
+        """mbs_reconstruct: MFS source strengths of every body (sum of n x nrhs)
+        from the boundary data v and the solved q_hat (Sec. 4.6)."""
+        a = _Arg(v, self.Mtot)
+        qa = _Arg(qhat, self.N)
+        out, p = _out_like(a, self.Nm)
+        self._check(_lib().mbs_reconstruct(self._h, a.nrhs, a.ptr, qa.ptr, p))
+        return _ret(out, a)
+
+    def evaluate_field_near(self, pts, qhat, qmfs):
+        """mbs_evaluate_field_near: scattered field at targets anywhere outside
+        the MFS curves, inside proxy surfaces included (Sec. 4.6)."""
+        a = _Arg(qhat, self.N)
+        ma = _Arg(qmfs, self.Nm)
+        if _is_torch(pts):
+            P = pts.to(torch.float64)
+            P = P if P.T.is_contiguous() else P.T.contiguous().T
+            P = P.T
+            pp = C.c_void_p(P.data_ptr())
+            M = pts.shape[0]
+        else:
+            P = _soa(pts)
+            pp = C.c_void_p(P.ctypes.data)
+            M = np.asarray(pts).shape[0]
+        out, p = _out_like(a, M)
+        self._check(_lib().mbs_evaluate_field_near(self._h, a.nrhs, M, pp, a.ptr, ma.ptr, p))
         return _ret(out, a)
 
     def inject_scattering(self, shape: int, skel, S, W=None):

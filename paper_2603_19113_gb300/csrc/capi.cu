@@ -35,6 +35,7 @@ struct ShapeHost {
     double eps_ach = 0;
     std::vector<int> skel;
     bool rhs_ok = true;  // false after a skeleton was injected without its W
+    bool injected = false;  // scattering data replaced by mbs_inject_scattering
     // device (owned by the context allocation list)
     double *dx = nullptr, *dy = nullptr, *dz = nullptr;
     double2 *AU = nullptr, *diagA = nullptr, *Zs = nullptr, *C = nullptr, *S64 = nullptr,
@@ -67,7 +68,7 @@ struct mbs_ctx {
     std::vector<ShapeHost> shapes;
     std::vector<mbs_body> bodies;
     int T = 0;
-    int64_t N = 0, Mtot = 0;
+    int64_t N = 0, Mtot = 0, Nm = 0;  // skeleton points, collocation points, MFS sources
     std::vector<int64_t> off, voff;
     std::vector<int> kb;  // per-body skeleton count
     std::vector<double> skel_world;  // dim * N SoA
@@ -92,6 +93,7 @@ struct mbs_ctx {
     const double2** d_S64p = nullptr;
     const float2** d_S32p = nullptr;
     RhsBody* d_rhsb = nullptr;
+    MfsBody* d_mfsb = nullptr;
     std::map<std::pair<int64_t, int>, int*> split_cache;  // (targets, nsplit) -> split_body
 
 
@@ -213,6 +215,7 @@ void free_geometry(mbs_ctx* c) {
     c->d_S64p = nullptr;
     c->d_S32p = nullptr;
     c->d_rhsb = nullptr;
+    c->d_mfsb = nullptr;
 }
 
 bool is_device_ptr(const void* p) {
@@ -1105,10 +1108,58 @@ mbs_status guarded(mbs_ctx* c, F&& f) {
     }
 }
 
+// For every target (SoA dim x M, host or device), the body whose proxy
+// surface strictly contains it, or -1; proxies are disjoint, so there is at
+// most one.  A hash grid of cell size = the largest proxy radius finds the
+// candidate bodies.  Throws MBS_ERR_ARG on a non-finite target.
+std::vector<int> proxy_bodies(mbs_ctx* c, const double* pts, int64_t M);
+
 bool finite_all(const double* p, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return false;
     return true;
+}
+
+std::vector<int> proxy_bodies(mbs_ctx* c, const double* pts, int64_t M) {
+    const int d = c->dim;
+    std::vector<double> hp((size_t)d * M);
+    if (is_device_ptr(pts))
+        MBS_CUDA_TRY(cudaMemcpy(hp.data(), pts, hp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(hp.data(), pts, hp.size() * sizeof(double));
+    if (!finite_all(hp.data(), hp.size())) throw MbsError{MBS_ERR_ARG, "non-finite target"};
+    double reach = 0;
+    for (int t = 0; t < c->T; ++t) reach = std::max(reach, c->shapes[c->bodies[t].shape].proxy_radius);
+    const double h = std::max(reach, 1e-12);
+    std::unordered_map<int64_t, std::vector<int>> grid;
+    auto key = [&](int64_t ix, int64_t iy, int64_t iz) {
+        return ((ix & 0x1FFFFF) << 42) | ((iy & 0x1FFFFF) << 21) | (iz & 0x1FFFFF);
+    };
+    for (int t = 0; t < c->T; ++t) {
+        const double* cc = c->bodies[t].c;
+        grid[key((int64_t)std::floor(cc[0] / h), (int64_t)std::floor(cc[1] / h),
+                 d == 3 ? (int64_t)std::floor(cc[2] / h) : 0)]
+            .push_back(t);
+    }
+    std::vector<int> tb((size_t)M, -1);
+    for (int64_t i = 0; i < M; ++i) {
+        double p3[3] = {hp[i], hp[(size_t)M + i], d == 3 ? hp[(size_t)2 * M + i] : 0.0};
+        const int64_t ix = (int64_t)std::floor(p3[0] / h), iy = (int64_t)std::floor(p3[1] / h),
+                      iz = d == 3 ? (int64_t)std::floor(p3[2] / h) : 0;
+        for (int64_t a = -1; a <= 1; ++a)
+            for (int64_t b2 = -1; b2 <= 1; ++b2)
+                for (int64_t e = (d == 3 ? -1 : 0); e <= (d == 3 ? 1 : 0); ++e) {
+                    auto it = grid.find(key(ix + a, iy + b2, iz + e));
+                    if (it == grid.end()) continue;
+                    for (int t : it->second) {
+                        const double pr = c->shapes[c->bodies[t].shape].proxy_radius;
+                        double r2 = 0;
+                        for (int q = 0; q < d; ++q) r2 += (p3[q] - c->bodies[t].c[q]) * (p3[q] - c->bodies[t].c[q]);
+                        if (r2 < pr * pr * (1.0 - 1e-12)) tb[i] = t;
+                    }
+                }
+    }
+    return tb;
 }
 
 void world_point(const mbs_body& B, int dim, const double* loc, double* out) {
@@ -1180,6 +1231,7 @@ void setup_layout(mbs_ctx* c) {
     const int T = c->T, d = c->dim;
     c->off.assign(T + 1, 0);
     c->voff.assign(T + 1, 0);
+    std::vector<int64_t> moff(T + 1, 0);
     c->kb.assign(T, 0);
     c->kmax = c->mmax = c->nmax = 0;
     for (int t = 0; t < T; ++t) {
@@ -1187,12 +1239,14 @@ void setup_layout(mbs_ctx* c) {
         c->kb[t] = s.k;
         c->off[t + 1] = c->off[t] + s.k;
         c->voff[t + 1] = c->voff[t] + s.m;
+        moff[t + 1] = moff[t] + s.n;
         c->kmax = std::max(c->kmax, s.k);
         c->mmax = std::max(c->mmax, s.m);
         c->nmax = std::max(c->nmax, s.n);
     }
     c->N = c->off[T];
     c->Mtot = c->voff[T];
+    c->Nm = moff[T];
     const int64_t N = c->N;
     std::vector<int> body(N);
     std::vector<float> loc32((size_t)d * N);
@@ -1262,6 +1316,7 @@ void setup_layout(mbs_ctx* c) {
         R.rankA = s.rankA;
         R.voff = c->voff[t];
         R.boff = c->off[t];
+        R.moff = moff[t];
         R.A = s.AU;
         R.diagA = s.diagA;
         R.permA = s.permA;
@@ -1273,6 +1328,17 @@ void setup_layout(mbs_ctx* c) {
     c->d_S64p = (const double2**)galloc<void*>(c, T);
     c->d_S32p = (const float2**)galloc<void*>(c, T);
     c->d_rhsb = galloc<RhsBody>(c, T);
+    std::vector<MfsBody> mb(T);
+    for (int t = 0; t < T; ++t) {
+        const ShapeHost& s = c->shapes[c->bodies[t].shape];
+        mb[t].y = s.dy;
+        mb[t].n = s.n;
+        mb[t].moff = moff[t];
+        for (int a = 0; a < 3; ++a) mb[t].c[a] = c->bodies[t].c[a];
+        for (int a = 0; a < 9; ++a) mb[t].R[a] = c->bodies[t].R[a];
+    }
+    c->d_mfsb = galloc<MfsBody>(c, T);
+    MBS_CUDA_TRY(cudaMemcpyAsync(c->d_mfsb, mb.data(), T * sizeof(MfsBody), cudaMemcpyHostToDevice, c->st));
     MBS_CUDA_TRY(cudaMemcpyAsync(c->d_k, c->kb.data(), T * sizeof(int), cudaMemcpyHostToDevice, c->st));
     MBS_CUDA_TRY(cudaMemcpyAsync((void*)c->d_S64p, s64.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c->st));
     MBS_CUDA_TRY(cudaMemcpyAsync((void*)c->d_S32p, s32.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c->st));
@@ -1288,7 +1354,7 @@ void refresh_layout(mbs_ctx* c) {
     std::vector<void*> keep;
     const void* lay[] = {c->d_body, c->d_off, c->d_loc32, c->d_xw64, c->d_centres, c->d_pair,
                          c->d_pair_phi0, c->d_k, c->d_S64p, c->d_S32p, c->d_rhsb,
-                         c->d_chunk_off, c->d_chunk_body};
+                         c->d_chunk_off, c->d_chunk_body, c->d_mfsb};
     for (void* p : c->geom_allocs) {
         bool is_lay = false;
         for (const void* q : lay)
@@ -1785,54 +1851,65 @@ mbs_status mbs_evaluate_field(mbs_ctx* c, int nrhs, int64_t M, const double* pts
         if (nrhs < 1 || M < 0 || (M > 0 && (!pts || !qhat || !u)))
             throw MbsError{MBS_ERR_ARG, "bad sizes or null pointer"};
         if (M == 0) return MBS_OK;
-        const int d = c->dim;
         // targets must lie on or outside every proxy surface
-        std::vector<double> hp((size_t)d * M);
-        if (is_device_ptr(pts))
-            MBS_CUDA_TRY(cudaMemcpy(hp.data(), pts, hp.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        else
-            std::memcpy(hp.data(), pts, hp.size() * sizeof(double));
-        if (!finite_all(hp.data(), hp.size())) throw MbsError{MBS_ERR_ARG, "non-finite target"};
-        double reach = 0;
-        for (int t = 0; t < c->T; ++t) reach = std::max(reach, c->shapes[c->bodies[t].shape].proxy_radius);
-        const double h = std::max(reach, 1e-12);
-        std::unordered_map<int64_t, std::vector<int>> grid;
-        auto key = [&](int64_t ix, int64_t iy, int64_t iz) {
-            return ((ix & 0x1FFFFF) << 42) | ((iy & 0x1FFFFF) << 21) | (iz & 0x1FFFFF);
-        };
-        for (int t = 0; t < c->T; ++t) {
-            const double* cc = c->bodies[t].c;
-            grid[key((int64_t)std::floor(cc[0] / h), (int64_t)std::floor(cc[1] / h),
-                     d == 3 ? (int64_t)std::floor(cc[2] / h) : 0)]
-                .push_back(t);
-        }
-        for (int64_t i = 0; i < M; ++i) {
-            double p3[3] = {hp[i], hp[(size_t)M + i], d == 3 ? hp[(size_t)2 * M + i] : 0.0};
-            const int64_t ix = (int64_t)std::floor(p3[0] / h), iy = (int64_t)std::floor(p3[1] / h),
-                          iz = d == 3 ? (int64_t)std::floor(p3[2] / h) : 0;
-            for (int64_t a = -1; a <= 1; ++a)
-                for (int64_t b2 = -1; b2 <= 1; ++b2)
-                    for (int64_t e = (d == 3 ? -1 : 0); e <= (d == 3 ? 1 : 0); ++e) {
-                        auto it = grid.find(key(ix + a, iy + b2, iz + e));
-                        if (it == grid.end()) continue;
-                        for (int t : it->second) {
-                            const double pr = c->shapes[c->bodies[t].shape].proxy_radius;
-                            double r2 = 0;
-                            for (int q = 0; q < d; ++q) r2 += (p3[q] - c->bodies[t].c[q]) * (p3[q] - c->bodies[t].c[q]);
-                            if (r2 < pr * pr * (1.0 - 1e-12))
-                                throw MbsError{MBS_ERR_NEAR_TARGET,
-                                               "target " + std::to_string(i) + " lies inside the proxy surface of body " +
-                                                   std::to_string(t)};
-                        }
-                    }
-        }
-        const double* dp = in_dev_real(c, pts, (size_t)d * M, "io_pts");
+        const std::vector<int> tb = proxy_bodies(c, pts, M);
+        for (int64_t i = 0; i < M; ++i)
+            if (tb[i] >= 0)
+                throw MbsError{MBS_ERR_NEAR_TARGET, "target " + std::to_string(i) +
+                                                        " lies inside the proxy surface of body " +
+                                                        std::to_string(tb[i])};
+        const double* dp = in_dev_real(c, pts, (size_t)c->dim * M, "io_pts");
         const double2* dq = in_dev(c, qhat, (size_t)c->N * nrhs, "io_q");
         OutBuf ou = out_dev(c, u, (size_t)M * nrhs, "io_u");
         int ns;
         int* sb = split_for(c, M, &ns);
         double2* part = scratch<double2>(c, "part_field", (size_t)ns * nrhs * M);
         launch_field_f64(glayout(c), c->kappa, M, dp, nrhs, dq, ou.dev, part, ns, sb, c->st);
+        finish_out(c, ou);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_reconstruct(mbs_ctx* c, int nrhs, const double* v, const double* qhat, double* qmfs) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (nrhs < 1 || !v || !qhat || !qmfs) throw MbsError{MBS_ERR_ARG, "bad nrhs or null pointer"};
+        for (const mbs_body& B : c->bodies)
+            if (c->shapes[B.shape].injected)
+                throw MbsError{MBS_ERR_STATE, "reconstruction needs the built scattering data (a shape was injected)"};
+        const double2* dv = in_dev(c, v, (size_t)c->Mtot * nrhs, "io_v");
+        const double2* dq = in_dev(c, qhat, (size_t)c->N * nrhs, "io_q");
+        OutBuf om = out_dev(c, qmfs, (size_t)c->Nm * nrhs, "io_qmfs");
+        double2* w_hat = scratch<double2>(c, "rec_w", (size_t)c->N * nrhs);
+        G64(c, nrhs, dq, w_hat);  // incoming field at every skeleton point from the other bodies
+        launch_recon(c->d_rhsb, c->T, nrhs, c->mmax, c->nmax, dv, c->Mtot, w_hat, c->N, om.dev, c->Nm,
+                     c->st);
+        finish_out(c, om);
+        return MBS_OK;
+    });
+}
+
+mbs_status mbs_evaluate_field_near(mbs_ctx* c, int nrhs, int64_t M, const double* pts,
+                                   const double* qhat, const double* qmfs, double* u) {
+    return guarded(c, [&]() {
+        require_built(c);
+        if (nrhs < 1 || M < 0 || (M > 0 && (!pts || !qhat || !qmfs || !u)))
+            throw MbsError{MBS_ERR_ARG, "bad sizes or null pointer"};
+        if (M == 0) return MBS_OK;
+        const std::vector<int> tb = proxy_bodies(c, pts, M);
+        int* d_tb = scratch<int>(c, "near_tb", (size_t)M);
+        MBS_CUDA_TRY(cudaMemcpyAsync(d_tb, tb.data(), (size_t)M * sizeof(int), cudaMemcpyHostToDevice, c->st));
+        const double* dp = in_dev_real(c, pts, (size_t)c->dim * M, "io_pts");
+        const double2* dq = in_dev(c, qhat, (size_t)c->N * nrhs, "io_q");
+        const double2* dm = in_dev(c, qmfs, (size_t)c->Nm * nrhs, "io_qmfs_in");
+        OutBuf ou = out_dev(c, u, (size_t)M * nrhs, "io_u");
+        int ns;
+        int* sb = split_for(c, M, &ns);
+        double2* part = scratch<double2>(c, "part_field", (size_t)ns * nrhs * M);
+        // skeleton sums of every body but the one whose proxy holds the target ...
+        launch_field_f64(glayout(c), c->kappa, M, dp, nrhs, dq, ou.dev, part, ns, sb, c->st, d_tb);
+        // ... plus that body's reconstructed MFS sources
+        launch_mfs_near(c->dim, M, dp, d_tb, c->d_mfsb, c->kappa, nrhs, dm, c->Nm, ou.dev, c->st);
         finish_out(c, ou);
         return MBS_OK;
     });
@@ -1850,6 +1927,7 @@ mbs_status mbs_inject_scattering(mbs_ctx* c, int shape, int k, const int* skel, 
             if (skel[i] < 0 || skel[i] >= s.m) throw MbsError{MBS_ERR_ARG, "skeleton index out of range"};
         const bool same = k == s.k && std::equal(skel, skel + k, s.skel.begin());
         s.rhs_ok = W != nullptr || (same && s.rhs_ok);
+        s.injected = true;
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
         s.k = k;
         s.skel.assign(skel, skel + k);

@@ -95,9 +95,24 @@ void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, flo
 void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, double2* y,
                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+// tbody (nullable): per target a body whose skeleton sources are left out (-1: none).
 void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
                       const double2* q, double2* u, double2* part, int nsplit,
-                      const int* d_split_body, cudaStream_t st);
+                      const int* d_split_body, cudaStream_t st, const int* tbody = nullptr);
+
+// MFS sources of one placed body (Sec. 4.6 reconstruction): y_world = c + R y_local.
+struct MfsBody {
+    const double* y;  // local MFS sources, SoA dim x n (the shape's device copy)
+    int n;
+    int64_t moff;     // first row of this body in q_mfs
+    double c[3];
+    double R[9];      // row-major rotation
+};
+// u(t) += sum_j phi(t - y_j^tau) q_mfs_tau,j for every target with tb[t] = tau >= 0;
+// pts SoA dim x M, u and q_mfs [nrhs][M] / [nrhs][Nm].
+void launch_mfs_near(int dim, int64_t M, const double* pts, const int* tb, const MfsBody* bodies,
+                     double kappa, int nrhs, const double2* qmfs, int64_t Nm, double2* u,
+                     cudaStream_t st);
 
 // Tensor-core FP32 G_hat (gumma.cu).  Sources are taken in chunks of
 // umma_chunk() that never straddle a body: chunk_off[T+1] (prefix sums of

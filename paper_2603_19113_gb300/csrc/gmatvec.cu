@@ -528,6 +528,40 @@ void launch_f64_dim(int64_t Nt, const double* tgt, const int* tbody, int64_t Ns,
     }
 }
 
+// Sec. 4.6: the field of body tau at a target inside its proxy surface from its
+// reconstructed MFS sources, added to u.  One thread per (target, RHS).
+template <int DIM>
+__global__ void mfs_near_kernel(const int64_t M, const double* __restrict__ pts,
+                                const int* __restrict__ tb, const MfsBody* __restrict__ bodies,
+                                const double kappa, const double2* __restrict__ qmfs,
+                                const int64_t Nm, double2* __restrict__ u) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= M) return;
+    const int t = tb[i];
+    if (t < 0) return;
+    const MfsBody& B = bodies[t];
+    double x[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) x[c] = pts[c * M + i] - B.c[c];
+    const double2* q = qmfs + (int64_t)r * Nm + B.moff;
+    double2 acc = u[(int64_t)r * M + i];
+    for (int j = 0; j < B.n; ++j) {
+        double r2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            double yw = 0.0;
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) yw = fma(B.R[3 * a + b], B.y[b * B.n + j], yw);
+            const double e = x[a] - yw;
+            r2 = fma(e, e, r2);
+        }
+        const double2 p = phi_f64<DIM>(kappa, sqrt(r2));
+        acc = cadd(acc, cmul(p, q[j]));
+    }
+    u[(int64_t)r * M + i] = acc;
+}
+
 }  // namespace
 
 void launch_pair_table(int dim, int T, const double* d_centres, const double* d_brad,
@@ -547,7 +581,7 @@ void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, flo
     // mac_path: 1 FP32 pipe, 2 mma.sync tensor-core multiply-add (3xTF32), 3 the
     // tcgen05 kernel of gumma.cu (the caller picks the path; 0 means 1 here).
     const int path = mac_path == 0 ? 1 : mac_path;
-    if (ev0) MBS_CUDA_TRY(cudaEventRecord(ev0, st));
+    if (ev0) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
     if (path == 3) {
         if (!U) throw MbsError{MBS_ERR_ARG, "launch_G_f32: the tcgen05 path needs its chunk layout"};
         launch_G_umma(L, *U, kappa, nrhs, q, part, nsplit, d_split_body, st);
@@ -556,7 +590,7 @@ void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, flo
     } else {
         launch_f32_dim<3>(L, K, nrhs, path, q, part, nsplit, d_split_body, st);
     }
-    if (ev1) MBS_CUDA_TRY(cudaEventRecord(ev1, st));
+    if (ev1) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<float2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
@@ -566,31 +600,45 @@ void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, do
                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
                   cudaEvent_t ev0, cudaEvent_t ev1) {
     if (L.N == 0 || nrhs == 0) return;
-    if (ev0) MBS_CUDA_TRY(cudaEventRecord(ev0, st));
+    if (ev0) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
     if (L.dim == 2)
         launch_f64_dim<2>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
     else
         launch_f64_dim<3>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
-    if (ev1) MBS_CUDA_TRY(cudaEventRecord(ev1, st));
+    if (ev1) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
 }
 
-// Field evaluation at arbitrary targets: the FP64 kernel without a body mask.
+// Field evaluation at arbitrary targets: the FP64 kernel, with an optional
+// per-target body whose skeleton sources are left out (near targets, whose own
+// body is represented by its MFS sources instead).
 void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
                       const double2* q, double2* u, double2* part, int nsplit,
-                      const int* d_split_body, cudaStream_t st) {
+                      const int* d_split_body, cudaStream_t st, const int* tbody) {
     if (M == 0 || nrhs == 0) return;
     if (L.dim == 2)
-        launch_f64_dim<2>(M, tgt, nullptr, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
+        launch_f64_dim<2>(M, tgt, tbody, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
     else
-        launch_f64_dim<3>(M, tgt, nullptr, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
+        launch_f64_dim<3>(M, tgt, tbody, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
     const int64_t len = M * nrhs;
     reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, u);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_mfs_near(int dim, int64_t M, const double* pts, const int* tb, const MfsBody* bodies,
+                     double kappa, int nrhs, const double2* qmfs, int64_t Nm, double2* u,
+                     cudaStream_t st) {
+    if (M == 0 || nrhs == 0) return;
+    dim3 g((unsigned)((M + 127) / 128), (unsigned)nrhs);
+    if (dim == 2)
+        mfs_near_kernel<2><<<g, 128, 0, st>>>(M, pts, tb, bodies, kappa, qmfs, Nm, u);
+    else
+        mfs_near_kernel<3><<<g, 128, 0, st>>>(M, pts, tb, bodies, kappa, qmfs, Nm, u);
     MBS_CHECK_LAUNCH();
 }

@@ -356,30 +356,13 @@ __global__ void __launch_bounds__(SBT) sbuild_phase2(SBuildJob* jobs, double rco
 // ----------------------------------------------------------------------------
 // right-hand side b_tau = Z* C A^+ v_tau, right to left, one CTA per (body, rhs)
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) rhs_kernel(const RhsBody* __restrict__ bodies, int T,
-                                                  const double2* __restrict__ v, int64_t Mtot,
-                                                  double2* __restrict__ b, int64_t N) {
-    __shared__ double rs[8], rs2[8];
-    extern __shared__ double2 sm[];
-    const int tau = blockIdx.x, r = blockIdx.y;
-    const RhsBody B = bodies[tau];
-    const int m = B.m, n = B.n, k = B.k;
-    double2* t = sm;          // m
-    double2* qm = sm + m;     // n
-    double2* q = sm + m + n;  // m
-    const double2* vin = v + (int64_t)r * Mtot + B.voff;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) t[i] = vin[i];
-    __syncthreads();
-    if (B.W) {  // injected W: b = W v
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            double2 s = make_double2(0.0, 0.0);
-            for (int l = 0; l < m; ++l) s = cadd(s, cmul(B.W[(int64_t)l * k + i], t[l]));
-            b[(int64_t)r * N + B.boff + i] = s;
-        }
-        return;
-    }
+// qm = A^+ t for one body with the stored pivoted QR of A truncated at rank
+// r_A (basic solution): t <- Q_A^H t by the Householder reflectors, back
+// substitution with R_A11, and the column permutation.  t (m) and qm (n) are
+// in shared memory; every thread of the block takes part.
+__device__ void apply_Apinv(const RhsBody& B, double2* t, double2* qm, double* rs, double* rs2) {
+    const int m = B.m, n = B.n;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // t = Q_A^H v
     for (int j = 0; j < B.rankA; ++j) {
         const double2* vj = B.A + (int64_t)j * m;
         double2 d = make_double2(0.0, 0.0);
@@ -406,14 +389,38 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsBody* __restrict__ bo
     if (threadIdx.x == 0) {
         for (int i = B.rankA - 1; i >= 0; --i) {
             double2 s = t[i];
-            for (int l = i + 1; l < B.rankA; ++l)
-                s = csub(s, cmul(B.A[(int64_t)l * m + i], t[l]));
+            for (int l = i + 1; l < B.rankA; ++l) s = csub(s, cmul(B.A[(int64_t)l * m + i], t[l]));
             const double2 d = B.diagA[i];
             t[i] = cscale(cmulc(d, s), 1.0 / cabs2(d));
         }
         for (int i = 0; i < B.rankA; ++i) qm[B.permA[i]] = t[i];
     }
     __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) rhs_kernel(const RhsBody* __restrict__ bodies, int T,
+                                                  const double2* __restrict__ v, int64_t Mtot,
+                                                  double2* __restrict__ b, int64_t N) {
+    __shared__ double rs[8], rs2[8];
+    extern __shared__ double2 sm[];
+    const int tau = blockIdx.x, r = blockIdx.y;
+    const RhsBody B = bodies[tau];
+    const int m = B.m, n = B.n, k = B.k;
+    double2* t = sm;          // m
+    double2* qm = sm + m;     // n
+    double2* q = sm + m + n;  // m
+    const double2* vin = v + (int64_t)r * Mtot + B.voff;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) t[i] = vin[i];
+    __syncthreads();
+    if (B.W) {  // injected W: b = W v
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int l = 0; l < m; ++l) s = cadd(s, cmul(B.W[(int64_t)l * k + i], t[l]));
+            b[(int64_t)r * N + B.boff + i] = s;
+        }
+        return;
+    }
+    apply_Apinv(B, t, qm, rs, rs2);
     // q = C q_mfs
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double2 s = make_double2(0.0, 0.0);
@@ -427,6 +434,30 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsBody* __restrict__ bo
         for (int l = 0; l < m; ++l) s = cadd(s, cmul(B.Zs[(int64_t)l * k + i], q[l]));
         b[(int64_t)r * N + B.boff + i] = s;
     }
+}
+
+// Sec. 4.6: q_mfs = A^+ (v - U w_hat), U(i, a) = Z*(a, i).
+__global__ void __launch_bounds__(256) recon_kernel(const RhsBody* __restrict__ bodies, int T,
+                                                    const double2* __restrict__ v, int64_t Mtot,
+                                                    const double2* __restrict__ w_hat, int64_t N,
+                                                    double2* __restrict__ qmfs, int64_t Nm) {
+    __shared__ double rs[8], rs2[8];
+    extern __shared__ double2 sm[];
+    const int tau = blockIdx.x, r = blockIdx.y;
+    const RhsBody B = bodies[tau];
+    const int m = B.m, n = B.n, k = B.k;
+    double2* t = sm;       // m
+    double2* qm = sm + m;  // n
+    const double2* vin = v + (int64_t)r * Mtot + B.voff;
+    const double2* wh = w_hat + (int64_t)r * N + B.boff;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 s = vin[i];
+        for (int a = 0; a < k; ++a) s = csub(s, cmul(B.Zs[(int64_t)i * k + a], wh[a]));
+        t[i] = s;
+    }
+    __syncthreads();
+    apply_Apinv(B, t, qm, rs, rs2);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) qmfs[(int64_t)r * Nm + B.moff + j] = qm[j];
 }
 
 void launch_sbuild_phase1(int dim, SBuildJob* d_jobs, int njobs, int pmax, double kappa,
@@ -464,5 +495,18 @@ void launch_rhs(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, co
                                           (int)sm));
     dim3 g((unsigned)T, (unsigned)nrhs);
     rhs_kernel<<<g, 256, sm, st>>>(d_bodies, T, v, Mtot, b, N);
+    MBS_CHECK_LAUNCH();
+}
+
+void launch_recon(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, const double2* v,
+                  int64_t Mtot, const double2* w_hat, int64_t N, double2* qmfs, int64_t Nm,
+                  cudaStream_t st) {
+    if (T == 0 || nrhs == 0) return;
+    const size_t sm = (size_t)(mmax + nmax) * sizeof(double2);
+    if (sm > 48 * 1024)
+        MBS_CUDA_TRY(cudaFuncSetAttribute(recon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm));
+    dim3 g((unsigned)T, (unsigned)nrhs);
+    recon_kernel<<<g, 256, sm, st>>>(d_bodies, T, v, Mtot, w_hat, N, qmfs, Nm);
     MBS_CHECK_LAUNCH();
 }

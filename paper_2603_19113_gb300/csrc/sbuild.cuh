@@ -37,6 +37,7 @@ struct RhsBody {
     int m, n, k, rankA;
     int64_t voff;   // first collocation row of this body in v
     int64_t boff;   // first skeleton row of this body in b
+    int64_t moff;   // first MFS source of this body in q_mfs
     const double2* A;      // reflectors + R_A (m x n, ld m)
     const double2* diagA;
     const int* permA;
@@ -50,3 +51,9 @@ void launch_sbuild_phase1(int dim, SBuildJob* d_jobs, int njobs, int pmax, doubl
 void launch_sbuild_phase2(SBuildJob* d_jobs, int njobs, int mmax, double rcond, cudaStream_t st);
 void launch_rhs(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, const double2* v,
                 int64_t Mtot, double2* b, int64_t N, cudaStream_t st);
+// q_mfs_tau = A_tau^+ (v_tau - U_tau w_hat_tau) for every body (Sec. 4.6), with
+// w_hat = G_hat q_hat the incoming field at the skeleton points ([nrhs][N]) and
+// U = (Z*)^T; q_mfs is [nrhs][Nm] with body tau at rows moff .. moff + n - 1.
+void launch_recon(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, const double2* v,
+                  int64_t Mtot, const double2* w_hat, int64_t N, double2* qmfs, int64_t Nm,
+                  cudaStream_t st);

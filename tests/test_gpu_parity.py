@@ -207,8 +207,13 @@ def test_block_gmres_graph_replay_matches_direct(pkg, prec):
     for graphs in (1, 0):
         ctx = pkg.Context(2, wl.kappa, precision=p, tol=1e-10, restart=4, cuda_graphs=graphs)
         ctx.build_scattering_matrices(wl)
-        q, info = ctx.solve(ctx.rhs(wl.boundary_data()))
+        b = ctx.rhs(wl.boundary_data())
+        ctx.profile(True)  # G_hat timing events inside the step graphs
+        q, info = ctx.solve(b)
+        kt = ctx.kernel_times()
         assert info["converged"] == 1 and info["inner_iterations"] > 8
+        assert kt["g32_launches"] + kt["g64_launches"] == info["matvecs_fp32"] + info["matvecs_fp64"]
+        assert kt["g32_ms"] + kt["g64_ms"] > 0
         out.append(q)
         ctx.close()
     assert np.array_equal(out[0], out[1])
@@ -273,6 +278,91 @@ def test_gpu_built_pipeline_three_bodies(pkg):
         assert info["converged"] == 1
         u = ctx.evaluate_field(tg, q)
         assert _rel(u, u_ref) < 1e-9, prec
+
+
+def _near_targets(wl, per_body=48, seed=7):
+    """Targets inside every proxy: on Gamma between collocation points (where
+    u + u_inc = 0 must hold) and in the annulus between Gamma and the proxy."""
+    from mbs_inputs.workloads import _BOUND, _curve
+    rng = np.random.default_rng(seed)
+    pts, on_gamma = [], []
+    for t in range(wl.T):
+        sh = wl.shapes[int(wl.body_shape[t])]
+        th = 2 * np.pi * (np.arange(sh.m) + 0.5) / sh.m
+        on = _curve(sh.name, th, sh.bound_radius / _BOUND[sh.name])[::max(1, sh.m // per_body)]
+        ang = rng.uniform(0, 2 * np.pi, per_body)
+        rad = rng.uniform(sh.bound_radius * 1.05, sh.proxy_radius * 0.98, per_body)
+        ring = np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+        for loc, flag in ((on, True), (ring, False)):
+            pts.append(wl.centres[t, :2] + loc @ wl.rots[t, :2, :2].T)
+            on_gamma.append(np.full(len(loc), flag))
+    return np.concatenate(pts, axis=0), np.concatenate(on_gamma)
+
+
+def test_near_field_reconstruction_matches_oracle(pkg):
+    """Sec. 4.6 on the GPU: q_mfs = A^+ (v - U G_hat q_hat) from the GPU-built
+    factors and the near field (MFS sources of the body whose proxy holds the
+    target, skeleton sums of the others) against the oracle's, on Gamma and in
+    the annuli between Gamma and the proxies; the GPU's own field also meets
+    the sound-soft condition on Gamma.  Far targets give exactly what
+    mbs_evaluate_field gives."""
+    wl = mi.tiny_2d(seed=0, T=4, kappa=6.0, nrhs=2, ks=(0, 0, 0), eps=1e-12)
+    for i, a in enumerate((1.0, 0.8, 0.9)):  # circles of three radii (resolved at m = 160)
+        wl.shapes[i] = mi.shape_2d("circle", 160, 80, 161, 1.3, scale=a, k=0, eps=1e-12)
+    ref = orc.solve_workload(wl)
+    qm_ref = orc.reconstruct_mfs(wl, ref["sdata"], ref["layout"], ref["q"], ref["v"])
+    tg, on_gamma = _near_targets(wl)
+    assert np.all(orc.proxy_body(wl, tg) >= 0)
+    u_ref = orc.field_near(wl, ref["sdata"], ref["layout"], ref["q"], qm_ref, tg)
+    far = mi.far_targets(wl, 64, mode="ring")
+    for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
+        ctx = pkg.Context(2, wl.kappa, precision=prec, tol=1e-11)
+        ctx.build_scattering_matrices(wl)
+        q, info = ctx.solve(ctx.rhs(ref["v"]))
+        qm = ctx.reconstruct(ref["v"], q)
+        assert qm.shape == (ctx.Nm, 2)
+        u = ctx.evaluate_field_near(tg, q, qm)
+        assert _rel(u, u_ref) < 1e-9, prec
+        on = tg[on_gamma]
+        u_on = u[on_gamma]
+        assert np.max(np.abs(u_on + wl.incident(on))) < 1e-8, prec
+        assert np.array_equal(ctx.evaluate_field_near(far, q, qm), ctx.evaluate_field(far, q))
+        with pytest.raises(pkg.MbsError):
+            ctx.evaluate_field(tg[:4], q)  # near targets need the reconstruction
+        ctx.close()
+
+
+def test_near_field_reconstruction_3d(pkg):
+    """The same in 3D (ellipsoids), targets between each surface and its proxy
+    sphere, against the oracle."""
+    wl = mi.tiny_3d(seed=2, T=3, kappa=2.0, nth=12, nph=20, p=241, k=0, eps=1e-11)
+    ref = orc.solve_workload(wl)
+    qm_ref = orc.reconstruct_mfs(wl, ref["sdata"], ref["layout"], ref["q"], ref["v"])
+    rng = np.random.default_rng(3)
+    pts = []
+    for t in range(wl.T):
+        sh = wl.shapes[int(wl.body_shape[t])]
+        d = rng.normal(size=(40, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        rad = rng.uniform(sh.bound_radius * 1.1, sh.proxy_radius * 0.97, 40)
+        pts.append(wl.centres[t] + d * rad[:, None])
+    tg = np.concatenate(pts)
+    assert np.all(orc.proxy_body(wl, tg) >= 0)
+    u_ref = orc.field_near(wl, ref["sdata"], ref["layout"], ref["q"], qm_ref, tg)
+    ctx = pkg.Context(3, wl.kappa, precision=pkg.PREC_FP64, tol=1e-11)
+    ctx.build_scattering_matrices(wl)
+    q, _ = ctx.solve(ctx.rhs(ref["v"]))
+    u = ctx.evaluate_field_near(tg, q, ctx.reconstruct(ref["v"], q))
+    assert _rel(u, u_ref) < 1e-8
+
+
+def test_reconstruction_refuses_injected_data(pkg):
+    wl = mi.config0()
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
+    q = _rand((ctx.N, 1), 2)
+    with pytest.raises(pkg.MbsError):
+        ctx.reconstruct(wl.boundary_data(), q)
+    ctx.close()
 
 
 # --------------------------------------------------------------------------
