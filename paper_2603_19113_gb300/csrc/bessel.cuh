@@ -22,6 +22,8 @@ __device__ __constant__ double c_f64_4F[MBS_F64_X4_DEG + 1] = MBS_F64_X4_F;
 __device__ __constant__ double c_f64_4G[MBS_F64_X4_DEG + 1] = MBS_F64_X4_G;
 __device__ __constant__ double c_f64_16F[MBS_F64_X16_DEG + 1] = MBS_F64_X16_F;
 __device__ __constant__ double c_f64_16G[MBS_F64_X16_DEG + 1] = MBS_F64_X16_G;
+__device__ __constant__ double c_f64_64F[MBS_F64_X64_DEG + 1] = MBS_F64_X64_F;
+__device__ __constant__ double c_f64_64G[MBS_F64_X64_DEG + 1] = MBS_F64_X64_G;
 
 template <int DEG>
 __device__ __forceinline__ float horner_f32(const float* c, float u) {
@@ -85,6 +87,58 @@ __device__ __forceinline__ double2 phi2d_f64(double x) {
     double s, c;
     sincos(x + 0.25 * MBS_PI + g, &s, &c);
     return make_double2(amp * c, amp * s);
+}
+
+// (i/4) H0(kappa r) in FP64 from the squared distance r2 (the form the G_hat
+// and field kernels use): one reciprocal square root gives 1/r for the fit
+// variable u = 2 XA / x - 1 = (2 XA / kappa) / r, and r itself after one
+// Newton step (r <- r + (r2 - r^2) / (2 r)), so the phase kappa r keeps the
+// accuracy of a rounded square root without a division.  Fits: degree 6 for
+// x >= 64, 10 for x >= 16, 20 for x >= 4, power series below.
+__device__ __forceinline__ double2 phi2d_f64_r2(double kappa, double r2) {
+    const double rinv = rsqrt(r2);
+    double r = r2 * rinv;
+    r = fma(0.5 * rinv, fma(-r, r, r2), r);
+    const double x = kappa * r;
+    double f, g;
+    if (x >= MBS_F64_X64_XA) {
+        const double u = (2.0 * MBS_F64_X64_XA / kappa) * rinv - 1.0;
+        f = horner_f64<MBS_F64_X64_DEG>(c_f64_64F, u);
+        g = horner_f64<MBS_F64_X64_DEG>(c_f64_64G, u);
+    } else if (x >= MBS_F64_X16_XA) {
+        const double u = (2.0 * MBS_F64_X16_XA / kappa) * rinv - 1.0;
+        f = horner_f64<MBS_F64_X16_DEG>(c_f64_16F, u);
+        g = horner_f64<MBS_F64_X16_DEG>(c_f64_16G, u);
+    } else if (x >= MBS_F64_X4_XA) {
+        const double u = (2.0 * MBS_F64_X4_XA / kappa) * rinv - 1.0;
+        f = horner_f64<MBS_F64_X4_DEG>(c_f64_4F, u);
+        g = horner_f64<MBS_F64_X4_DEG>(c_f64_4G, u);
+    } else {
+        return phi2d_f64(x);
+    }
+    // 0.25 * sqrt(2/pi) = 0.19947114020071633
+    const double amp = 0.19947114020071633 * f * rsqrt(x);
+    double s, c;
+    sincos(x + 0.25 * MBS_PI + g, &s, &c);
+    return make_double2(amp * c, amp * s);
+}
+
+// e^{i kappa r} / (4 pi r) from r2: 1/r by one reciprocal square root, r by
+// one Newton step.
+__device__ __forceinline__ double2 phi3d_f64_r2(double kappa, double r2) {
+    const double rinv = rsqrt(r2);
+    double r = r2 * rinv;
+    r = fma(0.5 * rinv, fma(-r, r, r2), r);
+    double s, c;
+    sincos(kappa * r, &s, &c);
+    const double a = rinv * (1.0 / (4.0 * MBS_PI));
+    return make_double2(a * c, a * s);
+}
+
+template <int DIM>
+__device__ __forceinline__ double2 phi_f64_r2(double kappa, double r2) {
+    if (DIM == 2) return phi2d_f64_r2(kappa, r2);
+    return phi3d_f64_r2(kappa, r2);
 }
 
 // phi in 3D at distance r, FP64.

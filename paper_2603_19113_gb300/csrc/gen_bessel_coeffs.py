@@ -24,6 +24,7 @@ FITS = [
     ("F32_X3", 3.0, 6, "float"),
     ("F64_X4", 4.0, 20, "double"),
     ("F64_X16", 16.0, 10, "double"),
+    ("F64_X64", 64.0, 6, "double"),
 ]
 
 

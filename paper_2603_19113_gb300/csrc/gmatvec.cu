@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(TPB) g_f64_kernel(
                         r21 = fma(e1, e1, r21);
                     }
                     double2 p0 = make_double2(0.0, 0.0), p1 = make_double2(0.0, 0.0);
-                    if (act0) p0 = phi_f64<DIM>(kappa, sqrt(r20));
-                    if (act1) p1 = phi_f64<DIM>(kappa, sqrt(r21));
+                    if (act0) p0 = phi_f64_r2<DIM>(kappa, r20);
+                    if (act1) p1 = phi_f64_r2<DIM>(kappa, r21);
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         const double2 qq = s_q[jj * NR + r];
@@ -556,7 +556,7 @@ __global__ void mfs_near_kernel(const int64_t M, const double* __restrict__ pts,
             const double e = x[a] - yw;
             r2 = fma(e, e, r2);
         }
-        const double2 p = phi_f64<DIM>(kappa, sqrt(r2));
+        const double2 p = phi_f64_r2<DIM>(kappa, r2);
         acc = cadd(acc, cmul(p, q[j]));
     }
     u[(int64_t)r * M + i] = acc;
