@@ -562,6 +562,18 @@ __global__ void mfs_near_kernel(const int64_t M, const double* __restrict__ pts,
     u[(int64_t)r * M + i] = acc;
 }
 
+// Timing event on st: inside a stream capture it must become an external
+// event-record node of the graph (recorded on every replay); outside a capture
+// the external flag is not allowed.
+void record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MBS_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+        MBS_CUDA_TRY(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+    else
+        MBS_CUDA_TRY(cudaEventRecord(e, st));
+}
+
 }  // namespace
 
 void launch_pair_table(int dim, int T, const double* d_centres, const double* d_brad,
@@ -581,7 +593,7 @@ void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, flo
     // mac_path: 1 FP32 pipe, 2 mma.sync tensor-core multiply-add (3xTF32), 3 the
     // tcgen05 kernel of gumma.cu (the caller picks the path; 0 means 1 here).
     const int path = mac_path == 0 ? 1 : mac_path;
-    if (ev0) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
+    if (ev0) record_event(ev0, st);
     if (path == 3) {
         if (!U) throw MbsError{MBS_ERR_ARG, "launch_G_f32: the tcgen05 path needs its chunk layout"};
         launch_G_umma(L, *U, kappa, nrhs, q, part, nsplit, d_split_body, st);
@@ -590,7 +602,7 @@ void launch_G_f32(const GLayout& L, double kappa, int nrhs, const float2* q, flo
     } else {
         launch_f32_dim<3>(L, K, nrhs, path, q, part, nsplit, d_split_body, st);
     }
-    if (ev1) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
+    if (ev1) record_event(ev1, st);
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<float2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
@@ -600,14 +612,14 @@ void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, do
                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
                   cudaEvent_t ev0, cudaEvent_t ev1) {
     if (L.N == 0 || nrhs == 0) return;
-    if (ev0) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal));
+    if (ev0) record_event(ev0, st);
     if (L.dim == 2)
         launch_f64_dim<2>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
     else
         launch_f64_dim<3>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
-    if (ev1) MBS_CUDA_TRY(cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal));
+    if (ev1) record_event(ev1, st);
     const int64_t len = L.N * nrhs;
     reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
