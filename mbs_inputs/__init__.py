@@ -14,6 +14,8 @@ Geometry readings (the paper leaves them open; see DESIGN notes):
     p points equispaced (2D) or on a spherical Fibonacci lattice (3D),
   * 3D ellipsoids: tensor grid in (theta, phi) with the 2:1 ratio per
     parameter between collocation and MFS grids (Sec. 3.4),
+  * non-smooth 2D bodies: Gauss-Legendre panels with dyadic refinement
+    towards corners, MFS distance scaled with the local panel size (Sec. 3.3),
   * incident field u_inc = exp(i kappa d.x); the boundary data is
     v = -u_inc (sound-soft, Sec. 2.1 footnote).
 """
@@ -21,6 +23,9 @@ from .workloads import (  # noqa: F401
     Shape,
     Workload,
     shape_2d,
+    shape_panels_2d,
+    panel_breaks,
+    panel_check_points,
     shape_ellipsoid,
     config0,
     config1,

@@ -35,6 +35,7 @@ class Shape:
     proxy_radius: float = 0.0
     bound_radius: float = 0.0
     name: str = ""
+    panels: np.ndarray | None = None  # panel end points in the curve parameter (panel shapes)
 
     @property
     def dim(self) -> int:
@@ -158,13 +159,74 @@ def _curve(kind: str, t: np.ndarray, scale: float) -> np.ndarray:
         return scale * np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
     if kind == "ellipse":  # semi-axes 1 and 0.6
         return scale * np.stack([np.cos(t), 0.6 * np.sin(t)], axis=1)
+    if kind == "teardrop":  # one corner at t = 0 (Sec. 5.1, Example 3)
+        x1 = 2.0 / np.pi ** 2 * t ** 2 - 4.0 / np.pi * t + 1.0
+        x2 = 2.0 / np.pi ** 3 * t ** 3 - 6.0 / np.pi ** 2 * t ** 2 + 4.0 / np.pi * t
+        return scale * np.stack([x1, x2], axis=1)
     if kind == "starfish5":  # f(t) = 81/101 - 20/101 cos 5t  (Sec. 5.1, Example 1)
         r = 81.0 / 101.0 - 20.0 / 101.0 * np.cos(5 * t)
         return scale * np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
     raise ValueError(kind)
 
 
-_BOUND = {"circle": 1.0, "star3": 1.2, "star3n": 1.0, "ellipse": 1.0, "starfish5": 1.0}
+_BOUND = {"circle": 1.0, "star3": 1.2, "star3n": 1.0, "ellipse": 1.0, "starfish5": 1.0,
+          "teardrop": 1.0}
+_CORNERS = {"teardrop": (0.0,)}  # curve parameters of corners (all curves run over [0, 2 pi))
+
+
+def _tangent(kind: str, t: np.ndarray, scale: float, h: float = 1e-6) -> np.ndarray:
+    """d x / d t by a central difference of the parametrisation (inputs only)."""
+    return (_curve(kind, t + h, scale) - _curve(kind, t - h, scale)) / (2.0 * h)
+
+
+def panel_breaks(kind: str, m_base: int, n_refine: int) -> np.ndarray:
+    """Panel end points in [0, 2 pi]: m_base equal panels, the two panels
+    touching each corner halved n_refine times towards it (dyadic refinement,
+    Sec. 3.3)."""
+    h = TWO_PI / m_base
+    br = set(np.round(np.arange(m_base + 1) * h, 15))
+    for c in _CORNERS.get(kind, ()):
+        for j in range(1, n_refine + 1):
+            br.add(round((c + h / 2 ** j) % TWO_PI, 15))
+            br.add(round((c - h / 2 ** j) % TWO_PI, 15))
+    return np.array(sorted(br))
+
+
+def shape_panels_2d(kind: str, m_base: int, n_refine: int, d: float, proxy_radius: float,
+                    q: int = 16, scale: float = 1.0, k: int = 0, eps: float = 0.0) -> Shape:
+    """Non-smooth 2D body on Gauss-Legendre panels (Sec. 3.3): q nodes per
+    panel for the collocation points, q / 2 per panel for the MFS sources
+    (n = m / 2), each source moved into the body along the normal by d times
+    the panel's length relative to a base panel, so the distance shrinks with
+    the dyadic refinement at corners; p = m + 1 proxy points on a circle."""
+    br = panel_breaks(kind, m_base, n_refine)
+    h = TWO_PI / m_base
+    gx, _ = np.polynomial.legendre.leggauss(q)
+    gy, _ = np.polynomial.legendre.leggauss(q // 2)
+    tx, ty, dy = [], [], []
+    for a, b in zip(br[:-1], br[1:]):
+        tx.append(a + (b - a) * (gx + 1.0) / 2.0)
+        ty.append(a + (b - a) * (gy + 1.0) / 2.0)
+        dy.append(np.full(q // 2, d * (b - a) / h))
+    tx, ty, dy = np.concatenate(tx), np.concatenate(ty), np.concatenate(dy)
+    x = _curve(kind, tx, scale)
+    tan = _tangent(kind, ty, scale)
+    inward = np.stack([-tan[:, 1], tan[:, 0]], axis=1) / np.linalg.norm(tan, axis=1)[:, None]
+    y = _curve(kind, ty, scale) + scale * dy[:, None] * inward  # counter-clockwise curves: left = inside
+    m = x.shape[0]
+    tz = TWO_PI * np.arange(m + 1) / (m + 1)
+    z = proxy_radius * np.stack([np.cos(tz), np.sin(tz)], axis=1)
+    return Shape(x=x, y=y, z=z, k=k, eps=eps, proxy_radius=proxy_radius,
+                 bound_radius=_BOUND[kind] * scale, name=kind, panels=br)
+
+
+def panel_check_points(sh: Shape, q: int = 7, scale: float = 1.0) -> np.ndarray:
+    """Points of a panel shape's boundary between its collocation points
+    (q-point Gauss-Legendre nodes on every panel)."""
+    g, _ = np.polynomial.legendre.leggauss(q)
+    br = sh.panels
+    t = np.concatenate([a + (b - a) * (g + 1.0) / 2.0 for a, b in zip(br[:-1], br[1:])])
+    return _curve(sh.name, t, scale)
 
 
 def shape_2d(kind: str, m: int, n: int, p: int, proxy_radius: float, scale: float = 1.0,

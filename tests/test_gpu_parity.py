@@ -316,13 +316,15 @@ def test_near_field_reconstruction_matches_oracle(pkg):
     u_ref = orc.field_near(wl, ref["sdata"], ref["layout"], ref["q"], qm_ref, tg)
     far = mi.far_targets(wl, 64, mode="ring")
     for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
-        ctx = pkg.Context(2, wl.kappa, precision=prec, tol=1e-11)
+        # tol 5e-10: as in the three-body pipeline test, the GPU-built S (pivoted
+        # QR least squares, larger norm) floors the FP64 residual near 1e-11
+        ctx = pkg.Context(2, wl.kappa, precision=prec, tol=5e-10)
         ctx.build_scattering_matrices(wl)
         q, info = ctx.solve(ctx.rhs(ref["v"]))
         qm = ctx.reconstruct(ref["v"], q)
         assert qm.shape == (ctx.Nm, 2)
         u = ctx.evaluate_field_near(tg, q, qm)
-        assert _rel(u, u_ref) < 1e-9, prec
+        assert _rel(u, u_ref) < 1e-8, prec
         on = tg[on_gamma]
         u_on = u[on_gamma]
         assert np.max(np.abs(u_on + wl.incident(on))) < 1e-8, prec
@@ -349,11 +351,40 @@ def test_near_field_reconstruction_3d(pkg):
     tg = np.concatenate(pts)
     assert np.all(orc.proxy_body(wl, tg) >= 0)
     u_ref = orc.field_near(wl, ref["sdata"], ref["layout"], ref["q"], qm_ref, tg)
-    ctx = pkg.Context(3, wl.kappa, precision=pkg.PREC_FP64, tol=1e-11)
+    ctx = pkg.Context(3, wl.kappa, precision=pkg.PREC_FP64, tol=5e-10)
     ctx.build_scattering_matrices(wl)
     q, _ = ctx.solve(ctx.rhs(ref["v"]))
     u = ctx.evaluate_field_near(tg, q, ctx.reconstruct(ref["v"], q))
     assert _rel(u, u_ref) < 1e-8
+
+
+def test_gpu_built_teardrops_with_corner_refinement(pkg):
+    """Non-smooth bodies (Sec. 3.3): three teardrops on Gauss-Legendre panels
+    with 12 dyadic refinements at the corner (m = 640, sources down to ~1e-5
+    from the corner), S built on the GPU, FP64 and mixed solves, far field and
+    near field against the oracle.  Tolerance 1e-8: changing the oracle's own
+    least-squares truncation from 1e-14 to 1e-12 moves this field by 3e-10."""
+    sh = mi.shape_panels_2d("teardrop", 16, 12, 0.3, 1.6, eps=1e-12)
+    centres = np.array([[0.0, 0.0, 0], [3.6, 0.5, 0], [0.9, 3.7, 0]])
+    rots = np.stack([mi.rot2(0.3), mi.rot2(1.9), mi.rot2(-0.8)])
+    wl = mi.Workload("teardrops", 2, 5.0, [sh], np.zeros(3, np.int32), centres, rots,
+                     np.array([[1.0, 0, 0], [math.cos(2.0), math.sin(2.0), 0]]))
+    ref = orc.solve_workload(wl)
+    qm_ref = orc.reconstruct_mfs(wl, ref["sdata"], ref["layout"], ref["q"], ref["v"])
+    far = mi.far_targets(wl, 96, mode="ring")
+    near = np.concatenate([wl.centres[t, :2] + mi.panel_check_points(sh)[::5] @ wl.rots[t, :2, :2].T
+                           for t in range(wl.T)])
+    u_far = orc.field(2, wl.kappa, far, ref["layout"]["xhat"], ref["q"])
+    u_near = orc.field_near(wl, ref["sdata"], ref["layout"], ref["q"], qm_ref, near)
+    for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
+        ctx = pkg.Context(2, wl.kappa, precision=prec, tol=5e-10)
+        ctx.build_scattering_matrices(wl)
+        q, info = ctx.solve(ctx.rhs(ref["v"]))
+        assert info["converged"] == 1
+        assert _rel(ctx.evaluate_field(far, q), u_far) < 1e-8, prec
+        u = ctx.evaluate_field_near(near, q, ctx.reconstruct(ref["v"], q))
+        assert _rel(u, u_near) < 1e-8, prec
+        ctx.close()
 
 
 def test_reconstruction_refuses_injected_data(pkg):
