@@ -390,3 +390,25 @@ def test_teardrop_dyadic_refinement_converges():
     assert errs[-1] < 3e-6
     assert all(b < 0.1 * a for a, b in zip(errs, errs[1:])), errs
     assert _relerr(far[2], far[3]) < 1e-4
+
+
+def test_near_field_sphere_closed_form_converges():
+    """One sound-soft sphere: the reconstructed MFS sources give the series
+    solution between the sphere and its proxy, with the error falling at the
+    MFS rate as the collocation grid is refined (12x24, 16x32, 20x40)."""
+    rng = np.random.default_rng(0)
+    d = rng.normal(size=(80, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    tg = d * rng.uniform(1.1, 1.5, 80)[:, None]
+    ue = sphere_scattered(1.0, 1.0, [0.0, 0.0, 1.0], tg)
+    errs = []
+    for nth, nph in ((12, 24), (16, 32), (20, 40)):
+        sh = mi.shape_ellipsoid(1, 1, 1, nth=nth, nph=nph, p=2 * nth * nph + 1, proxy_radius=1.6,
+                                eps=1e-11, mfs_scale=0.5)
+        wl = mi.Workload("sphere", 3, 1.0, [sh], np.zeros(1, np.int32), np.zeros((1, 3)),
+                         np.eye(3)[None].copy(), np.array([[0.0, 0.0, 1.0]]))
+        res = orc.solve_workload(wl)
+        qm = orc.reconstruct_mfs(wl, res["sdata"], res["layout"], res["q"], res["v"])
+        assert np.all(orc.proxy_body(wl, tg) == 0)
+        errs.append(_relerr(orc.field_near(wl, res["sdata"], res["layout"], res["q"], qm, tg)[:, 0], ue))
+    assert errs[-1] < 1e-5 and errs[1] < 0.3 * errs[0] and errs[2] < 0.3 * errs[1], errs
