@@ -95,7 +95,6 @@ def run_serving(a, pkg, mi):
         lat.append(res["t_end"] - res["t_submit"])
         done.append(res["t_end"])
     first = min(srv.poll(rid)["t_submit"] for _, rid in ids)
-    srv.close()
     lat = np.array(lat)
     waits, serv = [], []
     for r, rid in ids:
@@ -106,6 +105,7 @@ def run_serving(a, pkg, mi):
             print(f"served: rid={r.rid} dim={r.dim} T={r.T} N={res['N']} nrhs={r.nrhs} kappa={r.kappa:.1f} "
                   f"iterations={res['inner_iterations']} wait_s={waits[-1]:.2f} service_s={serv[-1]:.2f}",
                   file=sys.stderr)
+    srv.close()
     return {"requests": len(ids), "failed": fails,
             "mean_wait_s": float(np.mean(waits)) if waits else None,
             "mean_service_s": float(np.mean(serv)) if serv else None,
