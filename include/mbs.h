@@ -108,6 +108,8 @@ typedef struct mbs_solve_info {
     int matvecs_fp32;     /* FP32 operator applications (each covers all RHS) */
     int matvecs_fp64;     /* FP64 operator applications (each covers all RHS) */
     int converged;        /* 1 if every RHS reached tol */
+    int fp64_finish;      /* mixed: 1 if refinement stopped contracting (or ran out of sweeps)
+                             and FP64 GMRES, warm-started from the refined iterate, finished */
     double rel_residual;  /* max over RHS of the final FP64 relative residual */
     double seconds;       /* wall time of the call */
 } mbs_solve_info;

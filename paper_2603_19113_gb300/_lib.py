@@ -41,7 +41,8 @@ class mbs_body(C.Structure):
 class mbs_solve_info(C.Structure):
     _fields_ = [
         ("inner_iterations", C.c_int), ("sweeps", C.c_int), ("matvecs_fp32", C.c_int),
-        ("matvecs_fp64", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
+        ("matvecs_fp64", C.c_int), ("converged", C.c_int), ("fp64_finish", C.c_int),
+        ("rel_residual", C.c_double),
         ("seconds", C.c_double),
     ]
 

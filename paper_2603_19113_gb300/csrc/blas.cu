@@ -275,31 +275,43 @@ inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) 
 // otherwise *ok = 0 and R = I, so a triangular solve with it stays finite.
 __global__ void chol_small_kernel(const double2* __restrict__ G, int s, double2* __restrict__ R,
                                   double* __restrict__ ok) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double gmax = 0.0;
-    for (int i = 0; i < s; ++i) gmax = fmax(gmax, G[(int64_t)i * s + i].x);
-    for (int e = 0; e < s * s; ++e) R[e] = make_double2(0.0, 0.0);
-    bool good = true;
-    for (int j = 0; j < s && good; ++j) {
-        for (int i = 0; i <= j; ++i) {
-            double2 sum = G[(int64_t)j * s + i];  // G(i, j)
-            for (int k = 0; k < i; ++k)
-                sum = csub(sum, cmulc(R[(int64_t)i * s + k], R[(int64_t)j * s + k]));
-            if (i == j) {
-                if (!(sum.x > 1e-13 * gmax)) {
-                    good = false;
-                    break;
+    // G and R live in shared memory while one thread factors: every entry it
+    // reads back was just written, which through global memory is an L2 round
+    // trip per access.
+    __shared__ double2 s_g[16 * 16], s_r[16 * 16];
+    __shared__ int s_good;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        s_g[e] = G[e];
+        s_r[e] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double gmax = 0.0;
+        for (int i = 0; i < s; ++i) gmax = fmax(gmax, s_g[i * s + i].x);
+        bool good = true;
+        for (int j = 0; j < s && good; ++j) {
+            for (int i = 0; i <= j; ++i) {
+                double2 sum = s_g[j * s + i];  // G(i, j)
+                for (int k = 0; k < i; ++k) sum = csub(sum, cmulc(s_r[i * s + k], s_r[j * s + k]));
+                if (i == j) {
+                    if (!(sum.x > 1e-13 * gmax)) {
+                        good = false;
+                        break;
+                    }
+                    s_r[j * s + j] = make_double2(sqrt(sum.x), 0.0);
+                } else {
+                    const double d = s_r[i * s + i].x;
+                    s_r[j * s + i] = make_double2(sum.x / d, sum.y / d);
                 }
-                R[(int64_t)j * s + j] = make_double2(sqrt(sum.x), 0.0);
-            } else {
-                const double d = R[(int64_t)i * s + i].x;
-                R[(int64_t)j * s + i] = make_double2(sum.x / d, sum.y / d);
             }
         }
+        s_good = good ? 1 : 0;
+        *ok = good ? 1.0 : 0.0;
     }
-    if (!good)
-        for (int e = 0; e < s * s; ++e) R[e] = make_double2((e % (s + 1)) == 0 ? 1.0 : 0.0, 0.0);
-    *ok = good ? 1.0 : 0.0;
+    __syncthreads();
+    const bool good = s_good != 0;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x)
+        R[e] = good ? s_r[e] : make_double2((e % (s + 1)) == 0 ? 1.0 : 0.0, 0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,6 +490,173 @@ __global__ void __launch_bounds__(256) ts_trsm_kernel(V* __restrict__ B, const i
     }
 }
 
+// FP32 tall-skinny products for block widths kb <= 8 and even N: 16-byte
+// loads (two consecutive rows of one column), the new block staged once per
+// CTA in shared memory, and no cross-warp reduction in the Gram product.
+constexpr int TG_W = 8;       // warps per CTA
+constexpr int TG_A = 4;       // basis columns per warp
+constexpr int TG_ROWS = 256;  // rows per shared-memory stage of B
+constexpr int TU_ROWS = 64;   // rows per CTA of the update (two per lane)
+
+__device__ __forceinline__ float4 ldg4(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// One step of a warp reduce-scatter: 2*HALF values per lane become HALF,
+// lanes with bit MASK set keep the upper half.  The additions happen in an
+// order fixed by the lane index, so the result is reproducible.
+template <int HALF, int MASK>
+__device__ __forceinline__ void fold_half(float (&v)[64], int lane) {
+    const bool up = (lane & MASK) != 0;
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+        const float send = up ? v[i] : v[i + HALF];
+        const float keep = up ? v[i + HALF] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, MASK);
+    }
+}
+
+// partial[(b * ka + a) * nblk + blk] = sum over rows [blk*chunk, (blk+1)*chunk)
+// of conj(A_a) B_b.  Warp w of CTA (blk, y) owns columns a0 .. a0+3,
+// a0 = (8 y + w) * 4; per lane the sums run over its rows in order, then a
+// reduce-scatter leaves pair (a0 + lane / 8, lane % 8) on each lane.
+__global__ void __launch_bounds__(256, 2) ts_gram32_kernel(const float2* __restrict__ A, const int ka,
+                                                           const float2* __restrict__ B, const int kb,
+                                                           const int64_t N, const int64_t chunk,
+                                                           double2* __restrict__ partial,
+                                                           const int nblk) {
+    __shared__ float4 s_b[8][TG_ROWS / 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int blk = blockIdx.x;
+    const int a0 = (blockIdx.y * TG_W + warp) * TG_A;
+    const bool active = a0 < ka;
+    const int64_t n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+    float v[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = 0.f;
+    for (int64_t s0 = n0; s0 < n1; s0 += TG_ROWS) {
+        const int pairs = (int)(min((int64_t)TG_ROWS, n1 - s0) >> 1);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 8 * (TG_ROWS / 2); idx += blockDim.x) {
+            const int b = idx / (TG_ROWS / 2), p = idx - b * (TG_ROWS / 2);
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (b < kb && p < pairs) x = ldg4(B + (int64_t)b * N + s0 + 2 * p);
+            s_b[b][p] = x;
+        }
+        __syncthreads();
+        if (!active) continue;
+#pragma unroll 2
+        for (int pp = 0; pp < TG_ROWS / 64; ++pp) {
+            const int p = lane + 32 * pp;
+            if (p < pairs) {
+                float4 av[TG_A];
+#pragma unroll
+                for (int a = 0; a < TG_A; ++a)
+                    av[a] = (a0 + a < ka) ? ldg4(A + (int64_t)(a0 + a) * N + s0 + 2 * p)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const float4 bv = s_b[b][p];
+#pragma unroll
+                    for (int a = 0; a < TG_A; ++a) {
+                        float& re = v[(a * 8 + b) * 2];
+                        float& im = v[(a * 8 + b) * 2 + 1];
+                        re = fmaf(av[a].x, bv.x, re);
+                        re = fmaf(av[a].y, bv.y, re);
+                        re = fmaf(av[a].z, bv.z, re);
+                        re = fmaf(av[a].w, bv.w, re);
+                        im = fmaf(av[a].x, bv.y, im);
+                        im = fmaf(-av[a].y, bv.x, im);
+                        im = fmaf(av[a].z, bv.w, im);
+                        im = fmaf(-av[a].w, bv.z, im);
+                    }
+                }
+            }
+        }
+    }
+    if (!active) return;
+    fold_half<32, 16>(v, lane);
+    fold_half<16, 8>(v, lane);
+    fold_half<8, 4>(v, lane);
+    fold_half<4, 2>(v, lane);
+    fold_half<2, 1>(v, lane);
+    const int a = a0 + (lane >> 3), b = lane & 7;
+    if (a < ka && b < kb) partial[((int64_t)b * ka + a) * nblk + blk] = make_double2(v[0], v[1]);
+}
+
+// coef[a * 8 + b] = alpha H(a, b) in FP32 (H ka x kb column-major), zero for b >= kb
+__global__ void ts_coef32_kernel(const double2* __restrict__ H, const int ka, const int kb,
+                                 const double alpha, float2* __restrict__ coef) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ka * 8) return;
+    const int a = i >> 3, b = i & 7;
+    float2 c = make_float2(0.f, 0.f);
+    if (b < kb) {
+        const double2 h = H[(int64_t)b * ka + a];
+        c = make_float2((float)(alpha * h.x), (float)(alpha * h.y));
+    }
+    coef[i] = c;
+}
+
+// B_b += sum_a A_a coef(a, b) on rows [64 blockIdx.x, +64): lane = two rows,
+// warp w sums its share of the columns in order, the eight warp sums are
+// added in warp order.
+__global__ void __launch_bounds__(256) ts_update32_kernel(const float2* __restrict__ A, const int ka,
+                                                          const float2* __restrict__ coef,
+                                                          float2* __restrict__ B, const int kb,
+                                                          const int64_t N) {
+    __shared__ float4 s_red[TG_W][8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * TU_ROWS + 2 * lane;
+    const int per = (ka + TG_W - 1) / TG_W;
+    const int c0 = min(ka, warp * per), c1 = min(ka, c0 + per);
+    float acc[8][4];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.f;
+    if (r0 < N) {
+        const float4* __restrict__ c4 = reinterpret_cast<const float4*>(coef);
+#pragma unroll 4
+        for (int a = c0; a < c1; ++a) {
+            const float4 av = ldg4(A + (int64_t)a * N + r0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 h = __ldg(c4 + (int64_t)a * 4 + q);
+                float* x = acc[2 * q];
+                float* y = acc[2 * q + 1];
+                x[0] = fmaf(av.x, h.x, fmaf(-av.y, h.y, x[0]));
+                x[1] = fmaf(av.x, h.y, fmaf(av.y, h.x, x[1]));
+                x[2] = fmaf(av.z, h.x, fmaf(-av.w, h.y, x[2]));
+                x[3] = fmaf(av.z, h.y, fmaf(av.w, h.x, x[3]));
+                y[0] = fmaf(av.x, h.z, fmaf(-av.y, h.w, y[0]));
+                y[1] = fmaf(av.x, h.w, fmaf(av.y, h.z, y[1]));
+                y[2] = fmaf(av.z, h.z, fmaf(-av.w, h.w, y[2]));
+                y[3] = fmaf(av.z, h.w, fmaf(av.w, h.z, y[3]));
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) s_red[warp][b][lane] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+    __syncthreads();
+    const int b = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * TU_ROWS + 2 * lane;
+    if (b < kb && row < N) {
+        float4 t = s_red[0][b][lane];
+#pragma unroll
+        for (int w = 1; w < TG_W; ++w) {
+            const float4 u = s_red[w][b][lane];
+            t.x += u.x;
+            t.y += u.y;
+            t.z += u.z;
+            t.w += u.w;
+        }
+        float4* o = reinterpret_cast<float4*>(B + (int64_t)b * N + row);
+        float4 x = *o;
+        x.x += t.x;
+        x.y += t.y;
+        x.z += t.z;
+        x.w += t.w;
+        *o = x;
+    }
+}
+
 }  // namespace
 
 int mbs_num_sms() {
@@ -613,7 +792,30 @@ void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 // tall-skinny block products (block GMRES)
 // ---------------------------------------------------------------------------
-int ts_gram_blocks(int64_t N, int ka, int kb) {
+namespace {
+// the FP32 kernels need kb <= 8 and even N (16-byte loads of row pairs)
+bool ts_fast(bool f32, int kb, int64_t N) { return f32 && kb <= 8 && (N % 2) == 0; }
+
+// rows per Gram block of the FP32 kernel: a multiple of the stage, about
+// four CTAs per resident slot over the whole grid
+int64_t ts_gram32_chunk(int64_t N, int ka) {
+    const int64_t tiles = (ka + TG_W * TG_A - 1) / (TG_W * TG_A);
+    const int64_t want = std::max<int64_t>(1, (8LL * mbs_num_sms() + tiles - 1) / tiles);
+    const int64_t rows = (N + want - 1) / want;
+    return std::max<int64_t>(TG_ROWS, (rows + TG_ROWS - 1) / TG_ROWS * TG_ROWS);
+}
+
+void check_aligned16(const void* p, const char* what) {
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0)
+        throw MbsError{MBS_ERR_ARG, std::string(what) + ": operand not 16-byte aligned"};
+}
+}  // namespace
+
+int ts_gram_blocks(int64_t N, int ka, int kb, bool f32) {
+    if (ts_fast(f32, kb, N)) {
+        const int64_t chunk = ts_gram32_chunk(N, ka);
+        return (int)std::max<int64_t>(1, (N + chunk - 1) / chunk);
+    }
     const int64_t tiles = (int64_t)((ka + TSG_A - 1) / TSG_A) * ((kb + TSG_B - 1) / TSG_B);
     const int64_t want = (8LL * mbs_num_sms() + tiles - 1) / tiles;
     return (int)std::max<int64_t>(1, std::min<int64_t>((N + 2047) / 2048, want));
@@ -627,8 +829,20 @@ void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* 
         MBS_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)ka * kb * sizeof(double2), st));
         return;
     }
-    dim3 g((unsigned)nblk, (unsigned)((ka + TSG_A - 1) / TSG_A), (unsigned)((kb + TSG_B - 1) / TSG_B));
-    ts_gram_kernel<V><<<g, 256, 0, st>>>(A, ka, B, kb, N, scratch, nblk);
+    if (ts_fast(sizeof(V) == 8, kb, N)) {
+        const int64_t chunk = ts_gram32_chunk(N, ka);
+        if (nblk != (int)((N + chunk - 1) / chunk))
+            throw MbsError{MBS_ERR_ARG, "launch_ts_gram: block count does not match ts_gram_blocks"};
+        check_aligned16(A, "launch_ts_gram");
+        check_aligned16(B, "launch_ts_gram");
+        dim3 g((unsigned)nblk, (unsigned)((ka + TG_W * TG_A - 1) / (TG_W * TG_A)));
+        ts_gram32_kernel<<<g, 256, 0, st>>>(reinterpret_cast<const float2*>(A), ka,
+                                            reinterpret_cast<const float2*>(B), kb, N, chunk, scratch,
+                                            nblk);
+    } else {
+        dim3 g((unsigned)nblk, (unsigned)((ka + TSG_A - 1) / TSG_A), (unsigned)((kb + TSG_B - 1) / TSG_B));
+        ts_gram_kernel<V><<<g, 256, 0, st>>>(A, ka, B, kb, N, scratch, nblk);
+    }
     MBS_CHECK_LAUNCH();
     dots_finish_kernel<<<nblocks((int64_t)ka * kb, 128), 128, 0, st>>>(scratch, ka * kb, nblk, C);
     MBS_CHECK_LAUNCH();
@@ -636,13 +850,22 @@ void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* 
 
 template <typename V>
 void launch_ts_update(const V* A, int ka, const double2* H, double alpha, V* B, int kb, int64_t N,
-                      cudaStream_t st) {
+                      cudaStream_t st, float2* coef) {
     if (ka == 0 || kb == 0 || N == 0) return;
     if (kb > 16) throw MbsError{MBS_ERR_ARG, "launch_ts_update: more than 16 columns"};
-    if (kb <= 8)
+    if (coef && ts_fast(sizeof(V) == 8, kb, N)) {
+        check_aligned16(A, "launch_ts_update");
+        check_aligned16(B, "launch_ts_update");
+        check_aligned16(coef, "launch_ts_update");
+        ts_coef32_kernel<<<nblocks((int64_t)ka * 8, 256), 256, 0, st>>>(H, ka, kb, alpha, coef);
+        MBS_CHECK_LAUNCH();
+        ts_update32_kernel<<<(unsigned)((N + TU_ROWS - 1) / TU_ROWS), 256, 0, st>>>(
+            reinterpret_cast<const float2*>(A), ka, coef, reinterpret_cast<float2*>(B), kb, N);
+    } else if (kb <= 8) {
         ts_update_kernel<V, 8><<<nblocks(N), 256, 0, st>>>(A, ka, H, alpha, B, kb, N);
-    else
+    } else {
         ts_update_kernel<V, 16><<<nblocks(N), 256, 0, st>>>(A, ka, H, alpha, B, kb, N);
+    }
     MBS_CHECK_LAUNCH();
 }
 
@@ -662,9 +885,9 @@ template void launch_ts_gram<float2>(const float2*, int, const float2*, int, int
 template void launch_ts_gram<double2>(const double2*, int, const double2*, int, int64_t, double2*,
                                       double2*, int, cudaStream_t);
 template void launch_ts_update<float2>(const float2*, int, const double2*, double, float2*, int,
-                                       int64_t, cudaStream_t);
+                                       int64_t, cudaStream_t, float2*);
 template void launch_ts_update<double2>(const double2*, int, const double2*, double, double2*, int,
-                                        int64_t, cudaStream_t);
+                                        int64_t, cudaStream_t, float2*);
 template void launch_ts_trsm<float2>(float2*, int, int64_t, const double2*, cudaStream_t);
 template void launch_ts_trsm<double2>(double2*, int, int64_t, const double2*, cudaStream_t);
 

@@ -760,7 +760,7 @@ void from_host_cd(const std::vector<cd>& in, V* d, cudaStream_t st, std::vector<
 // [s^2, 2 s^2), and the two positive-definiteness flags in the next double2.
 template <typename V>
 void cholqr2_dev(mbs_ctx* c, V* W, int64_t N, int s, double2* Bs, double2* d_gram, double2* d_part) {
-    const int nb = ts_gram_blocks(N, s, s);
+    const int nb = ts_gram_blocks(N, s, s, sizeof(V) == 8);
     double* ok = reinterpret_cast<double*>(Bs + 2 * s * s);
     for (int pass = 0; pass < 2; ++pass) {
         double2* R = Bs + (size_t)pass * s * s;
@@ -865,14 +865,19 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
     const size_t nsmall = 2 * sq + 1 + 2 * (size_t)restart * sq;
     double2* Bs = scratch<double2>(c, "bg_small", nsmall);
     double2* d_gram = scratch<double2>(c, "bg_gram", sq);
-    double2* hb = pinned_stage(c, nsmall);
+    // two readback buffers: the host reduces step j while step j+1 runs
+    double2* hb0 = pinned_stage(c, 2 * nsmall);
+    double2* const hbs[2] = {hb0, hb0 + nsmall};
+    double2* hb = hbs[0];
+    constexpr bool f32 = sizeof(V) == 8;
     // partial sums of the Gram products (nblk * ka * s for every block width ka used)
     size_t part = 0;
     for (int j = 0; j < restart; ++j) {
         const int ka = (j + 1) * s;
-        part = std::max(part, (size_t)ts_gram_blocks(N, ka, s) * ka * s);
+        part = std::max(part, (size_t)ts_gram_blocks(N, ka, s, f32) * ka * s);
     }
     double2* d_part = scratch<double2>(c, "bg_part", part);
+    float2* d_coef = f32 ? scratch<float2>(c, "bg_coef", (size_t)restart * s * 8) : nullptr;
     double* d_inv = scratch<double>(c, "gm_inv", s);
     const std::vector<double> bn = norms<V>(c, b, s);
     if (x_zero) {
@@ -886,6 +891,7 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
     const int M = restart * s;         // columns of the block Hessenberg
     const int ldH = (restart + 1) * s;  // its rows
     std::vector<cd> H, G, Hcol, Rk, cs_, sn_;
+    std::vector<double> Tre, Tim;
     double prev_worst = 1e300;
     bool warm = false;
     while (true) {
@@ -912,6 +918,7 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         launch_scale<V>(r, d_inv, basis, N, s, c->st);
         std::vector<cd> Rq;
         cholqr2_dev<V>(c, basis, N, s, Bs, d_gram, d_part);
+        hb = hbs[0];
         MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1) * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
         if (!cholqr2_host(hb, s, Rq)) break;  // R0 numerically rank deficient
@@ -923,39 +930,55 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         sn_.assign((size_t)M * s, cd(0.0));
         int jdone = 0;
         bool breakdown = false;
-        for (int j = 0; j < restart && S.iters < maxit; ++j) {
+        // the step's device work, queued without host synchronisation: operator,
+        // block CGS2 (Hcol = V^H W; W -= V Hcol, twice), CholQR2 of the new block
+        // and one readback of both coefficient blocks and both factors into hbs[j % 2]
+        auto enqueue = [&](int j) {
             const int K = (j + 1) * s;
-            // the step's device work, queued without host synchronisation: operator,
-            // block CGS2 (Hcol = V^H W; W -= V Hcol, twice), CholQR2 of the new block
-            // and one readback of both coefficient blocks and both factors
-            auto enqueue = [&]() {
-                V* vj = basis + (size_t)j * NV;
-                apply_op<V>(c, s, vj, w);
-                double2* h1 = Bs + 2 * sq + 1;
-                double2* h2 = h1 + (size_t)K * s;
-                for (int pass = 0; pass < 2; ++pass) {
-                    double2* hp = pass == 0 ? h1 : h2;
-                    launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s), c->st);
-                    launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st);
-                }
-                V* vn = basis + (size_t)(j + 1) * NV;
-                MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
-                cholqr2_dev<V>(c, vn, N, s, Bs, d_gram, d_part);
-                MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1 + 2 * (size_t)K * s) * sizeof(double2),
-                                             cudaMemcpyDeviceToHost, c->st));
-            };
-            // after one direct step (autotuning, buffer allocation) the steps run
-            // from CUDA graphs captured once per context and step index
+            V* vj = basis + (size_t)j * NV;
+            apply_op<V>(c, s, vj, w);
+            double2* h1 = Bs + 2 * sq + 1;
+            double2* h2 = h1 + (size_t)K * s;
+            for (int pass = 0; pass < 2; ++pass) {
+                double2* hp = pass == 0 ? h1 : h2;
+                launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s, f32), c->st);
+                launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st, d_coef);
+            }
+            V* vn = basis + (size_t)(j + 1) * NV;
+            MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
+            cholqr2_dev<V>(c, vn, N, s, Bs, d_gram, d_part);
+            MBS_CUDA_TRY(cudaMemcpyAsync(hbs[j & 1], Bs, (2 * sq + 1 + 2 * (size_t)K * s) * sizeof(double2),
+                                         cudaMemcpyDeviceToHost, c->st));
+        };
+        // after one direct step (autotuning, buffer allocation) the steps run
+        // from CUDA graphs captured once per context and step index
+        auto launch_step = [&](int j) -> StepGraph* {
             StepGraph* sg = nullptr;
             if (warm && c->opt.cuda_graphs && !c->graphs_off) {
                 const std::array<int64_t, 8> key{(int64_t)sizeof(V), s, j, restart, (int64_t)(intptr_t)basis,
                                                  (int64_t)(intptr_t)w, (int64_t)(intptr_t)Bs,
-                                                 (int64_t)(intptr_t)hb};
-                sg = run_step_graph(c, key, sizeof(V) == 8 ? 0 : 1, enqueue);
+                                                 (int64_t)(intptr_t)hbs[j & 1]};
+                sg = run_step_graph(c, key, f32 ? 0 : 1, [&]() { enqueue(j); });
             }
-            if (!sg) enqueue();
+            if (!sg) enqueue(j);
+            return sg;
+        };
+        StepGraph* sg_next = nullptr;
+        bool pending = false;  // a queued step not yet reduced on the host
+        size_t mark32 = 0, mark64 = 0;
+        auto launch_next = [&](int j) {
+            mark32 = c->ev32.size();
+            mark64 = c->ev64.size();
+            sg_next = launch_step(j);
+            pending = true;
+        };
+        if (restart > 0 && S.iters < maxit) launch_next(0);
+        for (int j = 0; j < restart && S.iters < maxit; ++j) {
+            const int K = (j + 1) * s;
+            StepGraph* sg = sg_next;
+            pending = false;
+            MBS_CUDA_TRY(cudaStreamSynchronize(c->st));  // step j is complete
             S.matvecs++;
-            MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
             warm = true;
             if (sg && sg->e0) {
                 float ms = 0.f;
@@ -963,6 +986,12 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
                 c->graph_ms[sg->prec] += ms;
                 c->graph_n[sg->prec] += 1;
             }
+            // step j+1 depends on step j's device results only: it runs while the
+            // host reduces step j, and is discarded unless step j leaves the cycle
+            // open (its matvec is then not counted)
+            sg_next = nullptr;
+            if (j + 1 < restart && S.iters + 1 < maxit) launch_next(j + 1);
+            hb = hbs[j & 1];
             Hcol.assign((size_t)K * s, cd(0.0));
             for (size_t e = 0; e < (size_t)K * s; ++e) {
                 const double2 a1 = hb[2 * sq + 1 + e], a2 = hb[2 * sq + 1 + (size_t)K * s + e];
@@ -974,17 +1003,47 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             }
             S.iters++;
             jdone = j + 1;
-            // block column j of H: rows 0..K-1 from Hcol, rows K..K+s-1 from Rk
+            // block column j of H: rows 0..K-1 from Hcol, rows K..K+s-1 from Rk.  The
+            // rotations of earlier steps act on the s new columns alike: they are
+            // applied to all s together (column index fastest, real arithmetic).
+            const int nrow = K + s;
+            Tre.assign((size_t)nrow * s, 0.0);
+            Tim.assign((size_t)nrow * s, 0.0);
+            for (int a = 0; a < s; ++a) {
+                for (int i = 0; i < K; ++i) {
+                    Tre[(size_t)i * s + a] = Hcol[(size_t)a * K + i].real();
+                    Tim[(size_t)i * s + a] = Hcol[(size_t)a * K + i].imag();
+                }
+                for (int i = 0; i <= a; ++i) {
+                    Tre[(size_t)(K + i) * s + a] = Rk[(size_t)a * s + i].real();
+                    Tim[(size_t)(K + i) * s + a] = Rk[(size_t)a * s + i].imag();
+                }
+            }
+            for (int pc = 0; pc < j * s; ++pc)
+                for (int t = 0; t < s; ++t) {
+                    const int row = pc + s - t;  // rotation on rows (row-1, row)
+                    const cd cc = cs_[(size_t)pc * s + t], ss = sn_[(size_t)pc * s + t];
+                    const double cr = cc.real(), ci = cc.imag(), sr = ss.real(), si = ss.imag();
+                    double* __restrict__ ur = &Tre[(size_t)(row - 1) * s];
+                    double* __restrict__ ui = &Tim[(size_t)(row - 1) * s];
+                    double* __restrict__ vr = &Tre[(size_t)row * s];
+                    double* __restrict__ vi = &Tim[(size_t)row * s];
+                    for (int a = 0; a < s; ++a) {
+                        const double xr = ur[a], xi = ui[a], yr = vr[a], yi = vi[a];
+                        ur[a] = (cr * xr + ci * xi) + (sr * yr + si * yi);
+                        ui[a] = (cr * xi - ci * xr) + (sr * yi - si * yr);
+                        vr[a] = (cr * yr - ci * yi) - (sr * xr - si * xi);
+                        vi[a] = (cr * yi + ci * yr) - (sr * xi + si * xr);
+                    }
+                }
             for (int a = 0; a < s; ++a) {
                 const int col = j * s + a;
                 cd* hc = &H[(size_t)col * ldH];
-                for (int i = 0; i < K; ++i) hc[i] = Hcol[(size_t)a * K + i];
-                for (int i = 0; i <= a; ++i) hc[K + i] = Rk[(size_t)a * s + i];
-                // previous rotations (in generation order)
-                for (int pc = 0; pc < col; ++pc)
+                for (int i = 0; i < nrow; ++i) hc[i] = cd(Tre[(size_t)i * s + a], Tim[(size_t)i * s + a]);
+                // rotations of this step's earlier columns (in generation order)
+                for (int pc = j * s; pc < col; ++pc)
                     for (int t = 0; t < s; ++t) {
-                        const int row = pc + s - t;  // rotation on rows (row-1, row)
-                        if (row > (j + 1) * s + s - 1) continue;
+                        const int row = pc + s - t;
                         const cd cc = cs_[(size_t)pc * s + t], ss = sn_[(size_t)pc * s + t];
                         const cd u = hc[row - 1], v = hc[row];
                         hc[row - 1] = std::conj(cc) * u + std::conj(ss) * v;
@@ -1018,21 +1077,60 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             }
             if (conv || breakdown) break;
         }
-        // Y = R^{-1} G(0:jdone*s, :), X += V Y
+        if (pending) {
+            // the step queued past the end of the cycle is discarded: a direct
+            // launch's profiling events leave the lists (a graph's are only read
+            // when its step is reduced)
+            MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
+            if (!sg_next) {
+                for (size_t i = mark32; i < c->ev32.size(); ++i) {
+                    c->ev_pool.push_back(c->ev32[i].first);
+                    c->ev_pool.push_back(c->ev32[i].second);
+                }
+                for (size_t i = mark64; i < c->ev64.size(); ++i) {
+                    c->ev_pool.push_back(c->ev64[i].first);
+                    c->ev_pool.push_back(c->ev64[i].second);
+                }
+                c->ev32.resize(std::min(mark32, c->ev32.size()));
+                c->ev64.resize(std::min(mark64, c->ev64.size()));
+            }
+        }
+        // Y = R^{-1} G(0:jdone*s, :), X += V Y.  Column-oriented back substitution:
+        // once y_i is known, column i of R (contiguous) updates rows above i.
         const int Mj = jdone * s;
         std::vector<cd> Y((size_t)Mj * s, cd(0.0));
+        Tre.assign((size_t)Mj * s, 0.0);
+        Tim.assign((size_t)Mj * s, 0.0);
         for (int q = 0; q < s; ++q)
-            for (int i = Mj - 1; i >= 0; --i) {
-                cd sum = G[(size_t)q * ldH + i];
-                for (int l = i + 1; l < Mj; ++l) sum -= H[(size_t)l * ldH + i] * Y[(size_t)q * Mj + l];
-                const cd dgl = H[(size_t)i * ldH + i];
-                Y[(size_t)q * Mj + i] = std::abs(dgl) > 0 ? sum / dgl : cd(0.0);
+            for (int i = 0; i < Mj; ++i) {
+                Tre[(size_t)i * s + q] = G[(size_t)q * ldH + i].real();
+                Tim[(size_t)i * s + q] = G[(size_t)q * ldH + i].imag();
             }
+        std::vector<double> yr(s), yi(s);
+        for (int i = Mj - 1; i >= 0; --i) {
+            const cd* hcol = &H[(size_t)i * ldH];
+            const cd dgl = hcol[i];
+            for (int q = 0; q < s; ++q) {
+                const cd y = std::abs(dgl) > 0 ? cd(Tre[(size_t)i * s + q], Tim[(size_t)i * s + q]) / dgl : cd(0.0);
+                Y[(size_t)q * Mj + i] = y;
+                yr[q] = y.real();
+                yi[q] = y.imag();
+            }
+            for (int l = 0; l < i; ++l) {
+                const double hr = hcol[l].real(), hi = hcol[l].imag();
+                double* __restrict__ gr = &Tre[(size_t)l * s];
+                double* __restrict__ gi = &Tim[(size_t)l * s];
+                for (int q = 0; q < s; ++q) {
+                    gr[q] -= hr * yr[q] - hi * yi[q];
+                    gi[q] -= hr * yi[q] + hi * yr[q];
+                }
+            }
+        }
         if (Mj > 0) {
             double2* d_y = scratch<double2>(c, "bg_y", (size_t)M * s);
             std::vector<double2> stage;
             from_host_cd(Y, d_y, c->st, stage);
-            launch_ts_update<V>(basis, Mj, d_y, 1.0, x, s, N, c->st);
+            launch_ts_update<V>(basis, Mj, d_y, 1.0, x, s, N, c->st, d_coef);
         }
         bool est_conv = true;
         for (int q = 0; q < s; ++q) est_conv = est_conv && S.relres[q] <= tol;
@@ -1793,6 +1891,7 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
             }
             std::vector<double> sc(nrhs);
             double prev = 1e300;
+            bool stalled = false;
             while (true) {
                 const std::vector<double> rn = norms<double2>(c, r64, nrhs);
                 relmax = 0.0;
@@ -1806,8 +1905,13 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
                     conv = true;
                     break;
                 }
-                if (inf.sweeps >= o.max_sweeps || inf.inner_iterations >= o.max_iter) break;
-                if (relmax > 0.5 * prev) break;  // refinement no longer contracts
+                if (inf.inner_iterations >= o.max_iter) break;
+                // refinement no longer contracts: the FP32 operator is too inaccurate
+                // for this problem (e.g. large S of corner-refined bodies)
+                if (inf.sweeps >= o.max_sweeps || relmax > 0.5 * prev) {
+                    stalled = true;
+                    break;
+                }
                 prev = relmax;
                 for (int q = 0; q < nrhs; ++q) {
                     const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
@@ -1826,6 +1930,17 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
                 inf.matvecs_fp64++;
                 launch_sub<double2>(db, t64, r64, (int64_t)n, c->st);
                 inf.sweeps++;
+            }
+            if (stalled && inf.inner_iterations < o.max_iter) {
+                // finish in FP64 from the refined iterate
+                GmresStats S = krylov<double2>(c, nrhs, db, ox.dev, false, o.tol, o.restart,
+                                               o.max_iter - inf.inner_iterations, true);
+                inf.inner_iterations += S.iters;
+                inf.matvecs_fp64 += S.matvecs;
+                inf.fp64_finish = 1;
+                conv = S.converged;
+                relmax = 0.0;
+                for (double v : S.relres) relmax = std::max(relmax, v);
             }
         }
         finish_out(c, ox);

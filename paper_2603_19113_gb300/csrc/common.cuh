@@ -170,8 +170,11 @@ void launch_f32_to_f64(const float2* a, double2* b, int64_t n, cudaStream_t st);
 // Tall-skinny block products of block GMRES (fixed reduction order):
 // C = A^H B (ka x kb, column-major, FP64), B += alpha A H, B <- B R^{-1}
 // (R upper triangular, FP64).  ts_gram needs scratch of nblk * ka * kb
-// double2 with nblk = ts_gram_blocks(N, ka, kb); kb <= 16 for update/trsm.
-int ts_gram_blocks(int64_t N, int ka, int kb);
+// double2 with nblk = ts_gram_blocks(N, ka, kb, V is float2); kb <= 16 for
+// update/trsm.  With FP32 vectors, kb <= 8 and even N the products take the
+// 16-byte-load kernels; the update then needs coef, ka * 8 float2 of scratch
+// (without it the general kernel runs).
+int ts_gram_blocks(int64_t N, int ka, int kb, bool f32);
 // Cholesky G = R^H R of an s x s Hermitian matrix on the device (s <= 16);
 // *ok = 1, or 0 (and R = I) if G is not numerically positive definite.
 void launch_chol_small(const double2* G, int s, double2* R, double* ok, cudaStream_t st);
@@ -180,7 +183,7 @@ void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* 
                     double2* scratch, int nblk, cudaStream_t st);
 template <typename V>
 void launch_ts_update(const V* A, int ka, const double2* H, double alpha, V* B, int kb, int64_t N,
-                      cudaStream_t st);
+                      cudaStream_t st, float2* coef = nullptr);
 template <typename V>
 void launch_ts_trsm(V* B, int kb, int64_t N, const double2* R, cudaStream_t st);
 void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st);
