@@ -32,17 +32,24 @@ __device__ __forceinline__ const double2* sptr<double2>(const SBlocks& B, int t)
 constexpr int SA_RC = 8;  // right-hand sides per pass
 
 // One CTA per body; y_tau staged in shared memory SA_RC columns at a time.
+// With k < blockDim the columns of S_tau are split over P = blockDim / k
+// thread groups (P <= SA_P); their partial sums are added in group order.
+constexpr int SA_P = 8;
 template <typename V>
 __global__ void __launch_bounds__(256) sapply_kernel(const SBlocks B, const int64_t N,
                                                      const int nrhs, const V* __restrict__ x,
-                                                     const V* __restrict__ y, V* __restrict__ z) {
+                                                     const V* __restrict__ y, V* __restrict__ z,
+                                                     const int kmax) {
     using T = typename Acc<V>::T;
     extern __shared__ unsigned char smem_raw[];
-    V* s_y = reinterpret_cast<V*>(smem_raw);
     const int tau = blockIdx.x;
     const int k = B.k[tau];
     const int64_t o = B.off[tau];
     const V* __restrict__ S = sptr<V>(B, tau);
+    V* s_y = reinterpret_cast<V*>(smem_raw);  // [SA_RC][kmax]
+    V* s_part = s_y + (size_t)SA_RC * kmax;    // [P][SA_RC][k], P k <= blockDim.x
+    const int P = k > 0 ? max(1, min(SA_P, (int)blockDim.x / k)) : 1;
+    const int span = (k + P - 1) / P;
     for (int rc = 0; rc < nrhs; rc += SA_RC) {
         const int nr = min(SA_RC, nrhs - rc);
         __syncthreads();
@@ -51,18 +58,63 @@ __global__ void __launch_bounds__(256) sapply_kernel(const SBlocks B, const int6
             s_y[r * k + i] = y[(int64_t)(rc + r) * N + o + i];
         }
         __syncthreads();
+        if (P > 1) {
+            // thread (i, part): rows i, columns [part * span, +span) of S_tau
+            const int i = threadIdx.x % k, part = threadIdx.x / k;
+            if (part < P) {
+                T ar[SA_RC], ai[SA_RC];
+#pragma unroll
+                for (int r = 0; r < SA_RC; ++r) ar[r] = ai[r] = T(0);
+                const int j1 = min(k, (part + 1) * span);
+                for (int j = part * span; j < j1; ++j) {
+                    const V sv = S[(int64_t)j * k + i];
+#pragma unroll
+                    for (int r = 0; r < SA_RC; ++r) {
+                        if (r < nr) {
+                            const V v = s_y[r * k + j];
+                            ar[r] = fma(sv.x, v.x, fma(-sv.y, v.y, ar[r]));
+                            ai[r] = fma(sv.x, v.y, fma(sv.y, v.x, ai[r]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < SA_RC; ++r) {
+                    V pv;
+                    pv.x = ar[r];
+                    pv.y = ai[r];
+                    s_part[((size_t)part * SA_RC + r) * k + i] = pv;
+                }
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < k * nr; idx += blockDim.x) {
+                const int r = idx / k, i = idx - r * k;
+                T sr = T(0), si = T(0);
+                for (int q = 0; q < P; ++q) {
+                    const V pv = s_part[((size_t)q * SA_RC + r) * k + i];
+                    sr += pv.x;
+                    si += pv.y;
+                }
+                const int64_t g = (int64_t)(rc + r) * N + o + i;
+                V out;
+                const V xv = x[g];
+                out.x = xv.x + sr;
+                out.y = xv.y + si;
+                z[g] = out;
+            }
+            continue;
+        }
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             T ar[SA_RC], ai[SA_RC];
 #pragma unroll
             for (int r = 0; r < SA_RC; ++r) ar[r] = ai[r] = T(0);
             for (int j = 0; j < k; ++j) {
-                const V s = S[(int64_t)j * k + i];
+                const V sv = S[(int64_t)j * k + i];
 #pragma unroll
                 for (int r = 0; r < SA_RC; ++r) {
                     if (r < nr) {
                         const V v = s_y[r * k + j];
-                        ar[r] = fma(s.x, v.x, fma(-s.y, v.y, ar[r]));
-                        ai[r] = fma(s.x, v.y, fma(s.y, v.x, ai[r]));
+                        ar[r] = fma(sv.x, v.x, fma(-sv.y, v.y, ar[r]));
+                        ai[r] = fma(sv.x, v.y, fma(sv.y, v.x, ai[r]));
                     }
                 }
             }
@@ -138,13 +190,27 @@ __global__ void __launch_bounds__(256) dots_kernel(const V* __restrict__ basis, 
     }
 }
 
+// out[ir] = sum over blk of partial[ir * nblk + blk]: one warp per output,
+// each lane sums a fixed stride of the partials in order, then an xor tree
+// (every lane ends with the same, reproducible total).
 __global__ void dots_finish_kernel(const double2* __restrict__ partial, int count, int nblk,
                                    double2* __restrict__ out) {
-    const int ir = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ir = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (ir >= count) return;
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(int64_t)ir * nblk + b]);
-    out[ir] = s;
+    const double2* __restrict__ p = partial + (int64_t)ir * nblk;
+    double sx = 0.0, sy = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
+        const double2 v = p[b];
+        sx += v.x;
+        sy += v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) out[ir] = make_double2(sx, sy);
 }
 
 // w_r += sign * sum_i basis_{i,r} h[i * nrhs + r]
@@ -273,45 +339,55 @@ inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) 
 // FP64 by one thread: R upper triangular, zero below the diagonal.  *ok = 1
 // if every pivot exceeds 1e-13 times the largest diagonal entry of G;
 // otherwise *ok = 0 and R = I, so a triangular solve with it stays finite.
-__global__ void chol_small_kernel(const double2* __restrict__ G, int s, double2* __restrict__ R,
-                                  double* __restrict__ ok) {
-    // G and R live in shared memory while one thread factors: every entry it
-    // reads back was just written, which through global memory is an L2 round
-    // trip per access.
-    __shared__ double2 s_g[16 * 16], s_r[16 * 16];
-    __shared__ int s_good;
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        s_g[e] = G[e];
-        s_r[e] = make_double2(0.0, 0.0);
-    }
+// G = R^H R, right-looking: step k takes the pivot, scales row k of R by
+// one reciprocal and updates the trailing upper triangle in parallel (one
+// thread per entry, 16 x 16 at most); every entry is updated in the order of k.
+__global__ void __launch_bounds__(256) chol_small_kernel(const double2* __restrict__ G, int s,
+                                                         double2* __restrict__ R,
+                                                         double* __restrict__ ok) {
+    __shared__ double2 g[16 * 16];  // g[j * s + i] = G(i, j), overwritten by R(i, j)
+    __shared__ double s_inv, s_gmax;
+    __shared__ int s_bad;
+    const int t = threadIdx.x;
+    for (int e = t; e < s * s; e += blockDim.x) g[e] = G[e];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         double gmax = 0.0;
-        for (int i = 0; i < s; ++i) gmax = fmax(gmax, s_g[i * s + i].x);
-        bool good = true;
-        for (int j = 0; j < s && good; ++j) {
-            for (int i = 0; i <= j; ++i) {
-                double2 sum = s_g[j * s + i];  // G(i, j)
-                for (int k = 0; k < i; ++k) sum = csub(sum, cmulc(s_r[i * s + k], s_r[j * s + k]));
-                if (i == j) {
-                    if (!(sum.x > 1e-13 * gmax)) {
-                        good = false;
-                        break;
-                    }
-                    s_r[j * s + j] = make_double2(sqrt(sum.x), 0.0);
-                } else {
-                    const double d = s_r[i * s + i].x;
-                    s_r[j * s + i] = make_double2(sum.x / d, sum.y / d);
-                }
+        for (int i = 0; i < s; ++i) gmax = fmax(gmax, g[i * s + i].x);
+        s_gmax = gmax;
+        s_bad = 0;
+    }
+    const int ti = t % 16, tj = t / 16;  // this thread's entry (ti, tj) of the upper triangle
+    for (int k = 0; k < s; ++k) {
+        __syncthreads();
+        if (t == 0) {
+            const double d = g[k * s + k].x;
+            if (!(d > 1e-13 * s_gmax)) {
+                s_bad = 1;
+            } else {
+                const double r = sqrt(d);
+                g[k * s + k] = make_double2(r, 0.0);
+                s_inv = 1.0 / r;
             }
         }
-        s_good = good ? 1 : 0;
-        *ok = good ? 1.0 : 0.0;
+        __syncthreads();
+        if (s_bad) break;
+        if (t > k && t < s) {  // R(k, t) = G(k, t) / R(k, k)
+            const double2 v = g[t * s + k];
+            g[t * s + k] = make_double2(v.x * s_inv, v.y * s_inv);
+        }
+        __syncthreads();
+        if (tj < s && ti > k && ti <= tj)  // G(i, j) -= conj(R(k, i)) R(k, j)
+            g[tj * s + ti] = csub(g[tj * s + ti], cmulc(g[ti * s + k], g[tj * s + k]));
     }
     __syncthreads();
-    const bool good = s_good != 0;
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x)
-        R[e] = good ? s_r[e] : make_double2((e % (s + 1)) == 0 ? 1.0 : 0.0, 0.0);
+    const bool good = s_bad == 0;
+    for (int e = t; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        R[e] = good ? (i <= j ? g[e] : make_double2(0.0, 0.0))
+                    : make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    if (t == 0) *ok = good ? 1.0 : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -673,22 +749,22 @@ int mbs_num_sms() {
 void launch_sapply_f32(const SBlocks& B, int64_t N, int nrhs, const float2* x, const float2* y,
                        float2* z, int kmax, cudaStream_t st) {
     if (B.T == 0 || nrhs == 0) return;
-    const size_t sm = (size_t)kmax * SA_RC * sizeof(float2);
+    const size_t sm = (size_t)(kmax + 256) * SA_RC * sizeof(float2);
     if (sm > 48 * 1024)
         MBS_CUDA_TRY(cudaFuncSetAttribute(sapply_kernel<float2>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    sapply_kernel<float2><<<B.T, 256, sm, st>>>(B, N, nrhs, x, y, z);
+    sapply_kernel<float2><<<B.T, 256, sm, st>>>(B, N, nrhs, x, y, z, kmax);
     MBS_CHECK_LAUNCH();
 }
 
 void launch_sapply_f64(const SBlocks& B, int64_t N, int nrhs, const double2* x, const double2* y,
                        double2* z, int kmax, cudaStream_t st) {
     if (B.T == 0 || nrhs == 0) return;
-    const size_t sm = (size_t)kmax * SA_RC * sizeof(double2);
+    const size_t sm = (size_t)(kmax + 256) * SA_RC * sizeof(double2);
     if (sm > 48 * 1024)
         MBS_CUDA_TRY(cudaFuncSetAttribute(sapply_kernel<double2>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    sapply_kernel<double2><<<B.T, 256, sm, st>>>(B, N, nrhs, x, y, z);
+    sapply_kernel<double2><<<B.T, 256, sm, st>>>(B, N, nrhs, x, y, z, kmax);
     MBS_CHECK_LAUNCH();
 }
 
@@ -706,7 +782,7 @@ void launch_dots(const V* basis, int nvec, const V* w, int64_t N, int nrhs, doub
                                           (int)sm));
     dots_kernel<V><<<g, 256, sm, st>>>(basis, nvec, w, N, nrhs, scratch, nblk);
     MBS_CHECK_LAUNCH();
-    dots_finish_kernel<<<nblocks(nvec * nrhs, 128), 128, 0, st>>>(scratch, nvec * nrhs, nblk, out);
+    dots_finish_kernel<<<nblocks((int64_t)nvec * nrhs * 32, 256), 256, 0, st>>>(scratch, nvec * nrhs, nblk, out);
     MBS_CHECK_LAUNCH();
 }
 
@@ -844,7 +920,7 @@ void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* 
         ts_gram_kernel<V><<<g, 256, 0, st>>>(A, ka, B, kb, N, scratch, nblk);
     }
     MBS_CHECK_LAUNCH();
-    dots_finish_kernel<<<nblocks((int64_t)ka * kb, 128), 128, 0, st>>>(scratch, ka * kb, nblk, C);
+    dots_finish_kernel<<<nblocks((int64_t)ka * kb * 32, 256), 256, 0, st>>>(scratch, ka * kb, nblk, C);
     MBS_CHECK_LAUNCH();
 }
 
@@ -893,6 +969,6 @@ template void launch_ts_trsm<double2>(double2*, int, int64_t, const double2*, cu
 
 void launch_chol_small(const double2* G, int s, double2* R, double* ok, cudaStream_t st) {
     if (s < 1 || s > 16) throw MbsError{MBS_ERR_ARG, "launch_chol_small: 1 <= s <= 16"};
-    chol_small_kernel<<<1, 32, 0, st>>>(G, s, R, ok);
+    chol_small_kernel<<<1, 256, 0, st>>>(G, s, R, ok);
     MBS_CHECK_LAUNCH();
 }
