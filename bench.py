@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="mbs", choices=["mbs", "reference"])
     ap.add_argument("--tol", type=float, default=1e-11)
     ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--inner-tol", type=float, default=1e-6,
+                    help="relative tolerance of each FP32 inner solve of the mixed refinement")
     ap.add_argument("--targets", type=int, default=4096)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 time-to-solution solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -354,7 +356,7 @@ def run_mbs(a, ws, rank, local):
     tg_pin = torch.from_numpy(np.ascontiguousarray(tg_host.T)).pin_memory().T
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=1e-6, restart=a.restart,
+    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=a.inner_tol, restart=a.restart,
                 max_iter=50000, max_sweeps=12, stream=stream.cuda_stream, mac_path=a.mac)
     ctx = pkg.Context(2, wl.kappa, **opts)
 
@@ -499,7 +501,8 @@ def run_mbs(a, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "pairs_per_matvec": pairs_mv, "nrhs": nrhs,
-                       "field_targets": M, "l2": "256 MiB buffer written before every step",
+                       "field_targets": M, "restart": a.restart, "inner_tol": a.inner_tol,
+                       "l2": "256 MiB buffer written before every step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(1, e_steps),
                     "d2h_bytes_per_step": d2h // max(1, e_steps), "steps": e_steps},
