@@ -147,7 +147,71 @@ def rot_quat(q: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # shapes
 # ----------------------------------------------------------------------------
+# Piecewise curves of Sec. 5.1 (C-shapes and rods): segments of circular arcs
+# and straight lines, each a fixed fraction of the parameter range [0, 2 pi)
+# (the footnoted panel fractions, so that equal panels in t put those shares
+# of the base panels on each segment); the joints are refined like corners.
+_C_ALPHA = math.pi / 4  # half opening angle of the C-shape's cavity
+_ROD_A, _ROD_B = 0.8, 0.2  # rod: straight half length, cap radius (width 0.4)
+
+
+def _arc(cx, cy, r, a0, a1):
+    return ("arc", cx, cy, r, a0, a1)
+
+
+def _line(x0, y0, x1, y1):
+    return ("line", x0, y0, x1, y1)
+
+
+_PIECES = {
+    # outer arc (2/5), cap at -alpha (3/20), inner arc backwards (3/10), cap at +alpha (3/20)
+    "cshape": [(0.4, _arc(0.0, 0.0, 1.0, _C_ALPHA, TWO_PI - _C_ALPHA)),
+               (0.15, _arc(0.8 * math.cos(_C_ALPHA), -0.8 * math.sin(_C_ALPHA), 0.2,
+                           -_C_ALPHA, math.pi - _C_ALPHA)),
+               (0.3, _arc(0.0, 0.0, 0.6, TWO_PI - _C_ALPHA, _C_ALPHA)),
+               (0.15, _arc(0.8 * math.cos(_C_ALPHA), 0.8 * math.sin(_C_ALPHA), 0.2,
+                           math.pi + _C_ALPHA, TWO_PI + _C_ALPHA))],
+    # bottom side (4/11), right cap (3/22), top side (4/11), left cap (3/22)
+    "rod": [(4 / 11, _line(-_ROD_A, -_ROD_B, _ROD_A, -_ROD_B)),
+            (3 / 22, _arc(_ROD_A, 0.0, _ROD_B, -math.pi / 2, math.pi / 2)),
+            (4 / 11, _line(_ROD_A, _ROD_B, -_ROD_A, _ROD_B)),
+            (3 / 22, _arc(-_ROD_A, 0.0, _ROD_B, math.pi / 2, 1.5 * math.pi))],
+}
+
+
+def _piece_starts(kind: str) -> np.ndarray:
+    return TWO_PI * np.concatenate([[0.0], np.cumsum([f for f, _ in _PIECES[kind]])])
+
+
+def _piecewise(kind: str, t: np.ndarray, deriv: bool) -> np.ndarray:
+    """Point (or d/dt) of a piecewise curve at parameters t in [0, 2 pi)."""
+    t = np.mod(np.asarray(t, dtype=np.float64), TWO_PI)
+    st = _piece_starts(kind)
+    idx = np.clip(np.searchsorted(st, t, side="right") - 1, 0, len(_PIECES[kind]) - 1)
+    out = np.empty((t.size, 2))
+    for i, (frac, seg) in enumerate(_PIECES[kind]):
+        sel = idx == i
+        u = (t[sel] - st[i]) / (TWO_PI * frac)
+        du = 1.0 / (TWO_PI * frac)
+        if seg[0] == "arc":
+            _, cx, cy, r, a0, a1 = seg
+            a = a0 + (a1 - a0) * u
+            if deriv:
+                out[sel] = (r * (a1 - a0) * du) * np.stack([-np.sin(a), np.cos(a)], axis=1)
+            else:
+                out[sel] = np.stack([cx + r * np.cos(a), cy + r * np.sin(a)], axis=1)
+        else:
+            _, x0, y0, x1, y1 = seg
+            if deriv:
+                out[sel] = np.array([(x1 - x0) * du, (y1 - y0) * du])
+            else:
+                out[sel] = np.stack([x0 + (x1 - x0) * u, y0 + (y1 - y0) * u], axis=1)
+    return out
+
+
 def _curve(kind: str, t: np.ndarray, scale: float) -> np.ndarray:
+    if kind in _PIECES:
+        return scale * _piecewise(kind, t, False)
     if kind == "circle":
         r = np.ones_like(t)
         return scale * np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
@@ -170,12 +234,20 @@ def _curve(kind: str, t: np.ndarray, scale: float) -> np.ndarray:
 
 
 _BOUND = {"circle": 1.0, "star3": 1.2, "star3n": 1.0, "ellipse": 1.0, "starfish5": 1.0,
-          "teardrop": 1.0}
-_CORNERS = {"teardrop": (0.0,)}  # curve parameters of corners (all curves run over [0, 2 pi))
+          "teardrop": 1.0, "cshape": 1.0, "rod": _ROD_A + _ROD_B}
+# curve parameters of corners and of joints where the curvature jumps (all
+# curves run over [0, 2 pi))
+_CORNERS = {"teardrop": (0.0,),
+            "cshape": tuple(_piece_starts("cshape")[:-1]),
+            "rod": tuple(_piece_starts("rod")[:-1])}
 
 
 def _tangent(kind: str, t: np.ndarray, scale: float, h: float = 1e-6) -> np.ndarray:
-    """d x / d t by a central difference of the parametrisation (inputs only)."""
+    """d x / d t: exact on piecewise curves (a difference would straddle a
+    joint next to a deeply refined one), else a central difference of the
+    parametrisation (inputs only)."""
+    if kind in _PIECES:
+        return scale * _piecewise(kind, t, True)
     return (_curve(kind, t + h, scale) - _curve(kind, t - h, scale)) / (2.0 * h)
 
 
@@ -199,6 +271,10 @@ def shape_panels_2d(kind: str, m_base: int, n_refine: int, d: float, proxy_radiu
     (n = m / 2), each source moved into the body along the normal by d times
     the panel's length relative to a base panel, so the distance shrinks with
     the dyadic refinement at corners; p = m + 1 proxy points on a circle."""
+    if kind in _PIECES:
+        for f, _ in _PIECES[kind]:
+            if abs(f * m_base - round(f * m_base)) > 1e-9:
+                raise ValueError(f"{kind}: m_base = {m_base} does not put whole panels on every segment")
     br = panel_breaks(kind, m_base, n_refine)
     h = TWO_PI / m_base
     gx, _ = np.polynomial.legendre.leggauss(q)

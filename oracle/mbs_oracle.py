@@ -24,7 +24,7 @@ What it follows, step by step, in the paper's order and notation:
                  whose proxy surface x lies outside, MFS sums of the one it lies in
                                                                (Sec. 4.6)
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * pivot rule: largest remaining column norm, recomputed in full at every
     step; ties (norm >= (1 - 1e-10) * max) go to the lowest original index;
   * eps mode stops when the largest remaining column norm is <= eps times the

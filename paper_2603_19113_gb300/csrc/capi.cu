@@ -922,7 +922,9 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1) * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
         if (!cholqr2_host(hb, s, Rq)) break;  // R0 numerically rank deficient
-        H.assign((size_t)ldH * M, cd(0.0));
+        // every entry of H read below (rows < (j+2)s of block column j) is written in
+        // this cycle first: no clearing between cycles
+        if (H.size() < (size_t)ldH * M) H.resize((size_t)ldH * M);
         G.assign((size_t)ldH * s, cd(0.0));  // right-hand side of the small LS, column-major ldH
         for (int q = 0; q < s; ++q)
             for (int i = 0; i <= q; ++i) G[(size_t)q * ldH + i] = Rq[(size_t)q * s + i] * beta[q];
@@ -1106,8 +1108,8 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
                 Tre[(size_t)i * s + q] = G[(size_t)q * ldH + i].real();
                 Tim[(size_t)i * s + q] = G[(size_t)q * ldH + i].imag();
             }
-        std::vector<double> yr(s), yi(s);
         for (int i = Mj - 1; i >= 0; --i) {
+            double yr[16], yi[16];  // s <= 16; local arrays keep the update loop free of aliasing
             const cd* hcol = &H[(size_t)i * ldH];
             const cd dgl = hcol[i];
             for (int q = 0; q < s; ++q) {
