@@ -1,7 +1,8 @@
 """In-tree build of the CUDA library libmbs.so for sm_103a (GB300).
 
-Each translation unit is compiled by nvcc in parallel into ``_build/`` and the
-objects are linked into ``libmbs.so`` next to this file.  A rebuild happens
+Each translation unit (CUDA, and the host-only ``.cpp``) is compiled by nvcc in
+parallel into ``_build/`` and the objects are linked into ``libmbs.so`` next to
+this file.  A rebuild happens
 only when a source or header is newer than the library.
 """
 from __future__ import annotations
@@ -18,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmbs.so")
 SOURCES = ["capi.cu", "gmatvec.cu", "gumma.cu", "blas.cu", "sbuild.cu", "peaks.cu", "serve.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "blsq.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-diag-suppress", "177"]
@@ -35,7 +36,7 @@ def _nvcc() -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
     files.append(os.path.join(INCLUDE, "mbs.h"))
     return files
 
@@ -54,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *EXTRA.get(src, []), "-I", INCLUDE, "-c",
                os.path.join(CSRC, src), "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)

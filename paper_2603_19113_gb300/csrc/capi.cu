@@ -12,6 +12,7 @@
 #include <vector>
 
 
+#include "blsq.h"
 #include "common.cuh"
 #include "sbuild.cuh"
 
@@ -888,10 +889,8 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         S.matvecs++;
         launch_sub<V>(b, w, r, (int64_t)NV, c->st);
     }
-    const int M = restart * s;         // columns of the block Hessenberg
-    const int ldH = (restart + 1) * s;  // its rows
-    std::vector<cd> H, G, Hcol, Rk, cs_, sn_;
-    std::vector<double> Tre, Tim;
+    std::vector<cd> Hcol, Rk;
+    BlockLsq lsq;  // the small least-squares problem of each cycle (host)
     double prev_worst = 1e300;
     bool warm = false;
     while (true) {
@@ -922,14 +921,7 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
         MBS_CUDA_TRY(cudaMemcpyAsync(hb, Bs, (2 * sq + 1) * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
         if (!cholqr2_host(hb, s, Rq)) break;  // R0 numerically rank deficient
-        // every entry of H read below (rows < (j+2)s of block column j) is written in
-        // this cycle first: no clearing between cycles
-        if (H.size() < (size_t)ldH * M) H.resize((size_t)ldH * M);
-        G.assign((size_t)ldH * s, cd(0.0));  // right-hand side of the small LS, column-major ldH
-        for (int q = 0; q < s; ++q)
-            for (int i = 0; i <= q; ++i) G[(size_t)q * ldH + i] = Rq[(size_t)q * s + i] * beta[q];
-        cs_.assign((size_t)M * s, cd(1.0));
-        sn_.assign((size_t)M * s, cd(0.0));
+        lsq.start(s, restart, Rq.data(), beta.data());
         int jdone = 0;
         bool breakdown = false;
         // the step's device work, queued without host synchronisation: operator,
@@ -1005,76 +997,11 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             }
             S.iters++;
             jdone = j + 1;
-            // block column j of H: rows 0..K-1 from Hcol, rows K..K+s-1 from Rk.  The
-            // rotations of earlier steps act on the s new columns alike: they are
-            // applied to all s together (column index fastest, real arithmetic).
-            const int nrow = K + s;
-            Tre.assign((size_t)nrow * s, 0.0);
-            Tim.assign((size_t)nrow * s, 0.0);
-            for (int a = 0; a < s; ++a) {
-                for (int i = 0; i < K; ++i) {
-                    Tre[(size_t)i * s + a] = Hcol[(size_t)a * K + i].real();
-                    Tim[(size_t)i * s + a] = Hcol[(size_t)a * K + i].imag();
-                }
-                for (int i = 0; i <= a; ++i) {
-                    Tre[(size_t)(K + i) * s + a] = Rk[(size_t)a * s + i].real();
-                    Tim[(size_t)(K + i) * s + a] = Rk[(size_t)a * s + i].imag();
-                }
-            }
-            for (int pc = 0; pc < j * s; ++pc)
-                for (int t = 0; t < s; ++t) {
-                    const int row = pc + s - t;  // rotation on rows (row-1, row)
-                    const cd cc = cs_[(size_t)pc * s + t], ss = sn_[(size_t)pc * s + t];
-                    const double cr = cc.real(), ci = cc.imag(), sr = ss.real(), si = ss.imag();
-                    double* __restrict__ ur = &Tre[(size_t)(row - 1) * s];
-                    double* __restrict__ ui = &Tim[(size_t)(row - 1) * s];
-                    double* __restrict__ vr = &Tre[(size_t)row * s];
-                    double* __restrict__ vi = &Tim[(size_t)row * s];
-                    for (int a = 0; a < s; ++a) {
-                        const double xr = ur[a], xi = ui[a], yr = vr[a], yi = vi[a];
-                        ur[a] = (cr * xr + ci * xi) + (sr * yr + si * yi);
-                        ui[a] = (cr * xi - ci * xr) + (sr * yi - si * yr);
-                        vr[a] = (cr * yr - ci * yi) - (sr * xr - si * xi);
-                        vi[a] = (cr * yi + ci * yr) - (sr * xi + si * xr);
-                    }
-                }
-            for (int a = 0; a < s; ++a) {
-                const int col = j * s + a;
-                cd* hc = &H[(size_t)col * ldH];
-                for (int i = 0; i < nrow; ++i) hc[i] = cd(Tre[(size_t)i * s + a], Tim[(size_t)i * s + a]);
-                // rotations of this step's earlier columns (in generation order)
-                for (int pc = j * s; pc < col; ++pc)
-                    for (int t = 0; t < s; ++t) {
-                        const int row = pc + s - t;
-                        const cd cc = cs_[(size_t)pc * s + t], ss = sn_[(size_t)pc * s + t];
-                        const cd u = hc[row - 1], v = hc[row];
-                        hc[row - 1] = std::conj(cc) * u + std::conj(ss) * v;
-                        hc[row] = -ss * u + cc * v;
-                    }
-                // new rotations: zero rows col+s .. col+1 (bottom up)
-                for (int t = 0; t < s; ++t) {
-                    const int row = col + s - t;
-                    const cd u = hc[row - 1], v = hc[row];
-                    const double den = std::sqrt(std::norm(u) + std::norm(v));
-                    const cd cc = den > 0 ? u / den : cd(1.0), ss = den > 0 ? v / den : cd(0.0);
-                    cs_[(size_t)col * s + t] = cc;
-                    sn_[(size_t)col * s + t] = ss;
-                    hc[row - 1] = den;
-                    hc[row] = 0.0;
-                    for (int q = 0; q < s; ++q) {
-                        cd* gq = &G[(size_t)q * ldH];
-                        const cd gu = gq[row - 1], gv = gq[row];
-                        gq[row - 1] = std::conj(cc) * gu + std::conj(ss) * gv;
-                        gq[row] = -ss * gu + cc * gv;
-                    }
-                }
-            }
-            // residual of RHS q: norm of G rows (j+1)s .. (j+2)s-1
+            // block column j of the Hessenberg matrix: Hcol above, Rk below
+            lsq.add(j, Hcol.data(), Rk.data());
             bool conv = true;
             for (int q = 0; q < s; ++q) {
-                double rr = 0.0;
-                for (int i = (j + 1) * s; i < (j + 2) * s; ++i) rr += std::norm(G[(size_t)q * ldH + i]);
-                S.relres[q] = bn[q] > 0 ? std::sqrt(rr) / bn[q] : 0.0;
+                S.relres[q] = bn[q] > 0 ? lsq.residual(q) / bn[q] : 0.0;
                 conv = conv && S.relres[q] <= tol;
             }
             if (conv || breakdown) break;
@@ -1097,39 +1024,12 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
                 c->ev64.resize(std::min(mark64, c->ev64.size()));
             }
         }
-        // Y = R^{-1} G(0:jdone*s, :), X += V Y.  Column-oriented back substitution:
-        // once y_i is known, column i of R (contiguous) updates rows above i.
+        // Y = R^{-1} G over the steps of this cycle, X += V Y
         const int Mj = jdone * s;
-        std::vector<cd> Y((size_t)Mj * s, cd(0.0));
-        Tre.assign((size_t)Mj * s, 0.0);
-        Tim.assign((size_t)Mj * s, 0.0);
-        for (int q = 0; q < s; ++q)
-            for (int i = 0; i < Mj; ++i) {
-                Tre[(size_t)i * s + q] = G[(size_t)q * ldH + i].real();
-                Tim[(size_t)i * s + q] = G[(size_t)q * ldH + i].imag();
-            }
-        for (int i = Mj - 1; i >= 0; --i) {
-            double yr[16], yi[16];  // s <= 16; local arrays keep the update loop free of aliasing
-            const cd* hcol = &H[(size_t)i * ldH];
-            const cd dgl = hcol[i];
-            for (int q = 0; q < s; ++q) {
-                const cd y = std::abs(dgl) > 0 ? cd(Tre[(size_t)i * s + q], Tim[(size_t)i * s + q]) / dgl : cd(0.0);
-                Y[(size_t)q * Mj + i] = y;
-                yr[q] = y.real();
-                yi[q] = y.imag();
-            }
-            for (int l = 0; l < i; ++l) {
-                const double hr = hcol[l].real(), hi = hcol[l].imag();
-                double* __restrict__ gr = &Tre[(size_t)l * s];
-                double* __restrict__ gi = &Tim[(size_t)l * s];
-                for (int q = 0; q < s; ++q) {
-                    gr[q] -= hr * yr[q] - hi * yi[q];
-                    gi[q] -= hr * yi[q] + hi * yr[q];
-                }
-            }
-        }
+        std::vector<cd> Y;
+        lsq.solve(jdone, Y);
         if (Mj > 0) {
-            double2* d_y = scratch<double2>(c, "bg_y", (size_t)M * s);
+            double2* d_y = scratch<double2>(c, "bg_y", (size_t)restart * s * s);
             std::vector<double2> stage;
             from_host_cd(Y, d_y, c->st, stage);
             launch_ts_update<V>(basis, Mj, d_y, 1.0, x, s, N, c->st, d_coef);
