@@ -51,10 +51,8 @@ DF_HD dfl two_prod(float a, float b) {
 DF_HD dfl df_make(float hi) { return {hi, 0.f}; }
 
 // nearest double-float to a double
-DF_HD dfl df_from_double(double d) {
-    const float hi = (float)d;
-    const float lo = (float)(d - (double)hi);
-    return {hi, lo};
+DF_HD constexpr dfl df_from_double(double d) {
+    return {(float)d, (float)(d - (double)(float)d)};
 }
 
 DF_HD double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
