@@ -1,0 +1,110 @@
+"""The seeded synthetic workloads match their stated recipe: sizes, skeleton
+counts, pairs per matvec, incident fields, determinism, and the geometric
+guarantees the method needs (bounding circles/spheres apart by the stated gap,
+no body reaching into another body's proxy surface; Sec. 4.1 requires the
+sources of every other body to lie outside each proxy)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import mbs_inputs as mi
+
+
+def _min_pair_margin(wl, need):
+    """min over body pairs of |c_t - c_s| - need(t, s), with need a function of
+    the two bodies (checked on the 12 nearest neighbours of every body)."""
+    d = wl.dim
+    c = wl.centres[:, :d]
+    dist, idx = cKDTree(c).query(c, k=min(13, wl.T))
+    worst = np.inf
+    for t in range(wl.T):
+        for dd, s in zip(dist[t, 1:], idx[t, 1:]):
+            worst = min(worst, dd - need(t, s))
+    return worst
+
+
+def _rotations_ok(wl):
+    d = wl.dim
+    R = wl.rots[:, :d, :d]
+    eye = np.einsum("tij,tkj->tik", R, R)
+    return np.allclose(eye, np.eye(d)[None], atol=1e-12) and np.allclose(np.linalg.det(R), 1.0)
+
+
+def test_config0_recipe():
+    wl = mi.config0()
+    sh = wl.shapes[0]
+    assert (wl.T, sh.m, sh.n, sh.p, sh.k, wl.kappa, wl.nrhs) == (10, 128, 64, 129, 64, 10.0, 1)
+    assert sh.proxy_radius == 1.5 and sh.bound_radius == pytest.approx(1.2)
+    assert np.allclose(wl.directions[0], [1.0, 0.0, 0.0])
+    assert _min_pair_margin(wl, lambda t, s: 1.2 + 1.2 + 0.6) >= -1e-12  # gap 0.6
+
+
+def test_config1_recipe():
+    wl = mi.config1()
+    ks = np.array([wl.shapes[s].k for s in wl.body_shape])
+    N = int(ks.sum())
+    assert (wl.T, N, wl.kappa, wl.nrhs, len(wl.shapes)) == (1000, 64000, 40.0, 8, 3)
+    assert N * N - int(np.sum(ks ** 2)) == 4_091_904_000
+    for sh in wl.shapes:
+        assert (sh.m, sh.n, sh.p, sh.k, sh.proxy_radius) == (128, 64, 129, 64, 1.25)
+        assert np.max(np.linalg.norm(sh.x, axis=1)) <= 1.0 + 1e-12
+    ang = np.arctan2(wl.directions[:, 1], wl.directions[:, 0]) % (2 * np.pi)
+    assert np.allclose(np.sort(ang), 2 * np.pi * np.arange(8) / 8)
+    assert np.all(np.abs(wl.centres[:, :2] - 50.0) <= 50.0)
+    assert _rotations_ok(wl)
+    assert _min_pair_margin(wl, lambda t, s: 2.5) >= -1e-12          # bounding gap >= 0.5
+    assert _min_pair_margin(wl, lambda t, s: 1.25 + 1.0) > 0          # outside every proxy
+    assert np.array_equal(mi.config1().centres, wl.centres)           # seeded
+    assert not np.array_equal(mi.config1(seed=1).centres, wl.centres)
+
+
+def test_config2_recipe():
+    wl = mi.config2()
+    rho = np.array([sh.bound_radius for sh in wl.shapes])
+    ks = np.array([sh.k for sh in wl.shapes])
+    assert (wl.T, wl.kappa, wl.nrhs) == (10000, 20.0, 16)
+    assert np.all((rho >= 0.5) & (rho <= 1.5))
+    assert np.array_equal(ks, np.clip(np.round(3.5 * 20.0 * rho), 32, 128).astype(int))
+    assert ks.min() >= 35 and ks.max() <= 105
+    for sh, k, r in zip(wl.shapes[:200], ks[:200], rho[:200]):
+        assert (sh.m, sh.n, sh.p) == (2 * k, k, 2 * k + 1) and sh.proxy_radius == pytest.approx(r + 0.25)
+    assert _min_pair_margin(wl, lambda t, s: rho[t] + rho[s] + 0.5) >= -1e-9
+    assert _min_pair_margin(wl, lambda t, s: rho[t] + 0.25 + rho[s]) > 0
+
+
+def test_config3_recipe():
+    wl = mi.config3()
+    assert (wl.T, wl.dim, wl.kappa, wl.nrhs) == (2000, 3, 8.0, 4)
+    sh0 = wl.shapes[0]
+    assert (sh0.m, sh0.n, sh0.p, sh0.k) == (600, 150, 601, 300)
+    N = sum(sh.k for sh in wl.shapes)
+    assert N == 600_000 and N * N - 2000 * 300 ** 2 == 359_820_000_000
+    amax = np.array([sh.bound_radius for sh in wl.shapes])
+    assert np.all((amax >= 0.6) & (amax <= 1.0))
+    assert np.allclose(np.linalg.norm(wl.directions, axis=1), 1.0)
+    assert _rotations_ok(wl)
+    assert _min_pair_margin(wl, lambda t, s: amax[t] + 0.25 + amax[s]) > 0
+
+
+def test_serving_trace_recipe():
+    tr = mi.serving_trace()
+    assert len(tr) == 512
+    arr = np.array([r.arrival for r in tr])
+    assert np.all(np.diff(arr) > 0)
+    assert abs(np.mean(np.diff(arr)) - 1 / 20) < 0.15 / 20
+    T = np.array([r.T for r in tr])
+    assert T.min() >= 20 and T.max() <= 3000
+    frac2d = np.mean([r.dim == 2 for r in tr])
+    assert abs(frac2d - 0.7) < 0.07
+    assert all(5 <= r.kappa <= 50 and 1 <= r.nrhs <= 32 for r in tr)
+    assert [(r.T, r.dim, r.nrhs) for r in mi.serving_trace()] == [(r.T, r.dim, r.nrhs) for r in tr]
+
+
+def test_incident_field_and_boundary_data():
+    wl = mi.config0()
+    X = wl.collocation_world()
+    assert X.shape == (1280, 2)
+    v = wl.boundary_data()
+    assert np.allclose(v[:, 0], -np.exp(1j * 10.0 * X[:, 0]))
