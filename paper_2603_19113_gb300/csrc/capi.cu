@@ -1815,13 +1815,24 @@ mbs_status mbs_solve(mbs_ctx* c, int nrhs, const double* b, double* qhat, mbs_so
                     break;
                 }
                 prev = relmax;
+                // Block GMRES needs every column non-zero (a zero column makes the
+                // block rank deficient and ends the solve at once): right-hand sides
+                // that have converged stay in the block, where the correction only
+                // lowers their residual further; the lockstep solver freezes them.
+                const bool block = nrhs > 1 && nrhs <= 16 && o.block_krylov;
                 for (int q = 0; q < nrhs; ++q) {
                     const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
-                    sc[q] = (rel > o.tol && rn[q] > 0) ? 1.0 / rn[q] : 0.0;
+                    sc[q] = ((block || rel > o.tol) && rn[q] > 0) ? 1.0 / rn[q] : 0.0;
                 }
+                // The last sweep needs only the reduction that is left to reach tol
+                // (with a factor 2 of margin): inner tolerance max(inner_tol, 0.5 tol /
+                // residual), but always at least a 10x reduction so that the sweep
+                // contracts.
+                const double left = relmax > 0 ? 0.5 * o.tol / relmax : 0.0;
+                const double itol = std::max(o.inner_tol, std::min(0.1, left));
                 MBS_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
                 launch_f64_to_f32_scaled(r64, d_sc, r32, c->N, nrhs, c->st);
-                GmresStats S = krylov<float2>(c, nrhs, r32, d32, true, o.inner_tol, o.restart,
+                GmresStats S = krylov<float2>(c, nrhs, r32, d32, true, itol, o.restart,
                                              o.max_iter - inf.inner_iterations, false);
                 inf.inner_iterations += S.iters;
                 inf.matvecs_fp32 += S.matvecs;
