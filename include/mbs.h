@@ -180,9 +180,14 @@ mbs_status mbs_apply_G(mbs_ctx* ctx, int precision, int nrhs, const double* q, d
 
 /*
  * solve(v_hat) -> q_hat: GMRES on (I + S G_hat) q_hat = b (Sec. 2.4), in FP64
- * or as FP32 GMRES inside FP64 iterative refinement (precision option).
- * b: N x nrhs.  qhat: on entry the initial guess (all zeros allowed); on
- * exit the solution (the best iterate on MBS_ERR_NOCONV).  info nullable.
+ * or as FP32 GMRES inside FP64 iterative refinement (precision option).  In
+ * refinement every sweep solves the scaled FP64 residual in FP32 to
+ * max(inner_tol, min(0.1, 0.5 tol / residual)) (the last sweep only as far as
+ * tol still needs); when a sweep fails to halve the residual, or max_sweeps
+ * runs out, FP64 GMRES finishes from the refined iterate (info->fp64_finish).
+ * b: N x nrhs.  qhat: on entry the initial guess (all zeros allowed; a
+ * previous solve's result resumes it); on exit the solution (the best iterate
+ * on MBS_ERR_NOCONV).  info nullable.
  */
 mbs_status mbs_solve(mbs_ctx* ctx, int nrhs, const double* b, double* qhat, mbs_solve_info* info);
 
