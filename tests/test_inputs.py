@@ -108,3 +108,38 @@ def test_incident_field_and_boundary_data():
     assert X.shape == (1280, 2)
     v = wl.boundary_data()
     assert np.allclose(v[:, 0], -np.exp(1j * 10.0 * X[:, 0]))
+
+
+@pytest.mark.parametrize("kind,m_base,nref", [("teardrop", 16, 12), ("cshape", 40, 4), ("rod", 44, 4)])
+def test_panel_shapes_refine_at_corners_and_keep_sources_inside(kind, m_base, nref):
+    """Sec. 3.3: the panels touching every corner (or curvature joint) are
+    halved n_refine times towards it, so the smallest panels there have
+    length h / 2^n_refine; every MFS source lies strictly inside the curve
+    (winding number 1), as the method of fundamental solutions requires."""
+    from mbs_inputs import workloads as w
+    sh = mi.shape_panels_2d(kind, m_base, nref, 0.3 if kind == "teardrop" else 0.1, 1.6)
+    h = 2 * np.pi / m_base
+    br = sh.panels
+    lengths = np.diff(br)
+    for c in w._CORNERS[kind]:
+        for side in (+1, -1):
+            # the panel that ends (side -1) or starts (side +1) at the corner
+            t = c % (2 * np.pi)
+            if side > 0:
+                i = int(np.argmin(np.abs(br[:-1] - t)))
+                if t == 0.0:
+                    i = 0
+            else:
+                i = int(np.argmin(np.abs(br[1:] - (t if t > 0 else 2 * np.pi))))
+            assert lengths[i] == pytest.approx(h / 2 ** nref, rel=1e-9), (kind, c, side)
+    poly = w._curve(kind, np.linspace(0, 2 * np.pi, 20001)[:-1], 1.0)
+    assert np.all(_winding_number(poly, sh.y) == 1)
+    assert np.all(_winding_number(poly, 1.7 * sh.z / np.linalg.norm(sh.z, axis=1, keepdims=True)) == 0)
+
+
+def _winding_number(poly, pts):
+    """Winding number of a closed polygon (M, 2) around each point (K, 2)."""
+    a = poly[None, :, :] - pts[:, None, :]
+    b = np.roll(poly, -1, axis=0)[None, :, :] - pts[:, None, :]
+    ang = np.arctan2(a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0], np.sum(a * b, axis=-1))
+    return np.rint(ang.sum(axis=1) / (2 * np.pi)).astype(int)
