@@ -850,6 +850,14 @@ StepGraph* run_step_graph(mbs_ctx* c, const std::array<int64_t, 8>& key, int pre
     return &it->second;
 }
 
+// Block GMRES (the restarted GMRES of Sec. 2.4 with the s right-hand sides as
+// one block): step j applies the operator to the newest block of s basis
+// vectors, orthogonalises by block CGS2 and CholQR2 on the device, and reduces
+// the block Hessenberg least-squares problem on the host (BlockLsq) while the
+// device already runs step j+1.  Stops when every right-hand side reaches tol
+// (relative to its own |b|), at maxit steps, or when a restart cycle no longer
+// reduces the worst residual by 10 %.  verify: confirm convergence with the
+// true residual before returning.
 template <typename V>
 GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, int restart,
                   int maxit, bool verify) {
