@@ -143,3 +143,20 @@ def _winding_number(poly, pts):
     b = np.roll(poly, -1, axis=0)[None, :, :] - pts[:, None, :]
     ang = np.arctan2(a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0], np.sum(a * b, axis=-1))
     return np.rint(ang.sum(axis=1) / (2 * np.pi)).astype(int)
+
+
+def test_serving_requests_materialise_as_stated():
+    """A 2D request is the config1 construction at its own T, kappa and nrhs
+    (box side scaled with sqrt(T / 1000)); a 3D request is the config3
+    construction with nrhs unit directions."""
+    tr = mi.serving_trace()
+    r2 = next(r for r in tr if r.dim == 2 and r.T < 400)
+    r3 = next(r for r in tr if r.dim == 3 and r.T < 400)
+    w2, w3 = mi.request_workload(r2), mi.request_workload(r3)
+    assert (w2.dim, w2.T, w2.kappa, w2.nrhs) == (2, r2.T, r2.kappa, r2.nrhs)
+    assert all(sh.k == 64 and sh.m == 128 for sh in w2.shapes)
+    side = np.ptp(w2.centres[:, :2], axis=0).max()
+    assert side <= 100 * math.sqrt(r2.T / 1000) * 1.1 + 3.2
+    assert (w3.dim, w3.T, w3.kappa, w3.nrhs) == (3, r3.T, r3.kappa, r3.nrhs)
+    assert all(sh.k == 300 and sh.m == 600 for sh in w3.shapes)
+    assert np.allclose(np.linalg.norm(w3.directions, axis=1), 1.0)
