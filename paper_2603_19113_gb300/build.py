@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmbs.so")
 SOURCES = ["capi.cu", "gmatvec.cu", "gumma.cu", "blas.cu", "sbuild.cu", "peaks.cu", "serve.cu",
-           "noalloc.cu", "blsq.cpp"]
+           "noalloc.cu", "gdf.cu", "blsq.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-diag-suppress", "177"]

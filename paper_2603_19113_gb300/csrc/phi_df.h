@@ -104,17 +104,25 @@ struct DfFit {
 };
 
 // (i/4) H0(kappa r) for kappa r >= the smallest fit's xa; phase phi0 + kappa
-// (r - R) + g with phi0 = kappa R + pi / 4 mod 2 pi.  fits: nfit fits ordered
-// by decreasing xa.  Returns false below the last fit (the caller evaluates
-// those rare pairs otherwise).
+// (r - R) + g with phi0 = kappa R + pi / 4 mod 2 pi.  fits: nfit <= 3 fits
+// ordered by decreasing xa (selected with constant indices, so that a device
+// caller's fit table stays in registers).  Returns false below the last fit
+// (the caller evaluates those rare pairs otherwise).
 DF_HD bool phi2d_df(dfl kappa, dfl R, dfl s, dfl phi0, const DfFit* fits, int nfit, dfl& re, dfl& im) {
     dfl r, rinv, dr;
     df_split_r(R, s, r, rinv, dr);
     const dfl x = df_mul(kappa, r);
-    int k = 0;
-    while (k < nfit && x.hi < fits[k].xa) ++k;
-    if (k == nfit) return false;
-    const DfFit& F = fits[k];
+    DfFit F = fits[0];
+    bool found = false;
+#if defined(__CUDACC__)
+#pragma unroll
+#endif
+    for (int k = 0; k < 3; ++k)
+        if (k < nfit && !found && x.hi >= fits[k].xa) {
+            F = fits[k];
+            found = true;
+        }
+    if (!found) return false;
     // u = (2 xa / kappa) / r - 1
     const dfl u = df_add_f(df_mul(df_div(df_make(2.0f * F.xa), kappa), rinv), -1.0f);
     const dfl f = df_horner(F.fhi, F.flo, F.deg, u);
