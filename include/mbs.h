@@ -82,6 +82,9 @@ typedef struct mbs_options {
                             0: heuristic shape */
     int cuda_graphs;     /* 1 (default): after one direct step, the device work of each block-GMRES step is
                             captured once per context and step index and replayed as a CUDA graph; 0: launch directly */
+    int fp64_kernel;     /* FP64-accurate G_hat (FP64 solves, refinement residuals, apply calls): 0 (default)
+                            on the FP64 pipe; 1 in double-float arithmetic on the FP32 pipe, with FP64 work only
+                            per body pair (agrees with 0 to ~1e-13 relative; not yet timed) */
 } mbs_options;
 
 typedef struct mbs_shape {
@@ -118,7 +121,7 @@ typedef struct mbs_ctx mbs_ctx;
 
 /* Fill *opt with defaults: FP64, tol 1e-11, inner_tol 1e-6, restart 60,
  * max_iter 20000, max_sweeps 8, ls_rcond 1e-14, stream NULL, no budget,
- * automatic G_hat kernel, autotuning and CUDA graphs on. */
+ * automatic G_hat kernel, autotuning and CUDA graphs on, FP64 G_hat on the FP64 pipe. */
 void mbs_default_options(mbs_options* opt);
 
 /* Create a context for dimension dim (2 or 3) and wavenumber kappa > 0

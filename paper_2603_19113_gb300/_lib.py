@@ -22,7 +22,7 @@ class mbs_options(C.Structure):
         ("restart", C.c_int), ("max_iter", C.c_int), ("max_sweeps", C.c_int),
         ("ls_rcond", C.c_double), ("stream", C.c_void_p), ("hbm_budget", C.c_size_t),
         ("tile_override", C.c_int), ("block_krylov", C.c_int), ("mac_path", C.c_int),
-        ("autotune", C.c_int), ("cuda_graphs", C.c_int),
+        ("autotune", C.c_int), ("cuda_graphs", C.c_int), ("fp64_kernel", C.c_int),
     ]
 
 

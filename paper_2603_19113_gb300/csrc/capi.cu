@@ -492,6 +492,21 @@ void G64(mbs_ctx* c, int nrhs, const double2* x, double2* y) {
         e1 = take_event(c);
         c->ev64.emplace_back(e0, e1);
     }
+    if (c->opt.fp64_kernel == 1) {
+        // double-float arithmetic on the FP32 pipe (gdf.cu); the events bracket
+        // the kernel and its split reduction
+        auto rec = [&](cudaEvent_t e) {
+            if (!e) return;
+            if (c->capturing)
+                MBS_CUDA_TRY(cudaEventRecordWithFlags(e, c->st, cudaEventRecordExternal));
+            else
+                MBS_CUDA_TRY(cudaEventRecord(e, c->st));
+        };
+        rec(e0);
+        launch_G_df(glayout(c), c->d_centres, c->kappa, nrhs, x, y, part, ns, sb, c->st);
+        rec(e1);
+        return;
+    }
     launch_G_f64(glayout(c), c->kappa, nrhs, x, y, part, ns, sb, c->st, e0, e1);
 }
 
@@ -1087,6 +1102,8 @@ void validate_options(const mbs_options& o) {
         throw MbsError{MBS_ERR_ARG, "invalid tolerance / restart / iteration options"};
     if (o.mac_path < 0 || o.mac_path > 3)
         throw MbsError{MBS_ERR_ARG, "mac_path must be 0, 1, 2 or 3"};
+    if (o.fp64_kernel < 0 || o.fp64_kernel > 1)
+        throw MbsError{MBS_ERR_ARG, "fp64_kernel must be 0 or 1"};
 }
 
 template <typename F>
@@ -1546,6 +1563,7 @@ void mbs_default_options(mbs_options* o) {
     o->mac_path = 0;
     o->autotune = 1;
     o->cuda_graphs = 1;
+    o->fp64_kernel = 0;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {

@@ -96,7 +96,7 @@ void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, do
                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // FP64-accurate G_hat in double-float arithmetic on the FP32 pipe (gdf.cu);
-// d_centres: [T][3] body centres (FP64).  No entry point dispatches to it yet.
+// d_centres: [T][3] body centres (FP64).  Selected by mbs_options.fp64_kernel = 1.
 void launch_G_df(const GLayout& L, const double* d_centres, double kappa, int nrhs, const double2* q,
                  double2* y, double2* part, int nsplit, const int* d_split_body, cudaStream_t st);
 // tbody (nullable): per target a body whose skeleton sources are left out (-1: none).

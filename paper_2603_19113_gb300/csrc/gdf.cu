@@ -13,7 +13,7 @@
 // the FP64 power series.  The building blocks are checked on the host against
 // the oracle's FP64 matvec (tests/test_gdf.py); on a GB300 the kernel agrees
 // with the FP64 kernel to 1.5e-13 (2D with and without the series fallback,
-// 3D).  No entry point dispatches to it yet.
+// 3D).  Selected by mbs_options.fp64_kernel = 1.
 #include "bessel.cuh"
 #include "common.cuh"
 #include "gdf_core.h"

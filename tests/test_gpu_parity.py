@@ -112,6 +112,39 @@ def test_G_3d_fp64_and_fp32(pkg, nrhs):
     assert _nrel(ctx.apply_G(q, pkg.PREC_FP32), ref) < 2e-5
 
 
+_DF_CASES = {
+    "2d": lambda: mi.tiny_2d(seed=1, T=9, kappa=6.0, ks=(24, 37, 50)),
+    "2d_small_kappa_r": lambda: mi.tiny_2d(seed=2, T=9, kappa=2.0, ks=(30, 41), spacing=2.9),
+    "3d": lambda: mi.tiny_3d(seed=0, T=5, kappa=3.0, nth=10, nph=14, p=141, k=70),
+}
+
+
+@pytest.mark.parametrize("case", list(_DF_CASES))
+def test_G_fp64_double_float_kernel(pkg, case):
+    """The FP64-accurate G_hat in double-float arithmetic on the FP32 pipe
+    (fp64_kernel = 1) against the oracle at the FP64-pipe kernel's bound: 2D in
+    the fitted range and below it (the FP64 series), 3D; N not a multiple of
+    the 128-target tile, 5 right-hand sides."""
+    wl = _DF_CASES[case]()
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, fp64_kernel=1)
+    q = _rand((ctx.N, 5), 21)
+    ref = orc.G_dense(wl.dim, wl.kappa, lay["xhat"], lay["body"]) @ q
+    assert _rel(ctx.apply_G(q, pkg.PREC_FP64), ref) < 1e-12
+
+
+def test_mixed_solve_with_double_float_residuals(pkg):
+    """Iterative refinement whose FP64 residuals come from the double-float
+    kernel converges to the oracle's solution."""
+    wl = mi.config0()
+    ref = orc.solve_workload(wl)
+    tg = mi.far_targets(wl, 128, mode="ring")
+    u_ref = orc.field(2, wl.kappa, tg, ref["layout"]["xhat"], ref["q"])
+    ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, precision=pkg.PREC_MIXED, tol=1e-11, fp64_kernel=1)
+    q, info = ctx.solve(ref["b"])
+    assert info["converged"] == 1
+    assert _rel(ctx.evaluate_field(tg, q), u_ref) < 1e-9
+
+
 def test_apply_operator_matches_oracle(pkg):
     wl = mi.config0()
     ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl)
