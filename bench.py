@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="mbs", choices=["mbs", "reference"])
     ap.add_argument("--tol", type=float, default=1e-11)
     ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--fp64-kernel", type=int, default=0, choices=[0, 1],
+                    help="FP64-accurate G_hat: 0 on the FP64 pipe, 1 in double-float on the FP32 pipe")
     ap.add_argument("--inner-tol", type=float, default=1e-4,
                     help="relative tolerance of each FP32 inner solve of the mixed refinement "
                          "(1e-4 reaches 1e-11 in 3 sweeps with the fewest inner iterations)")
@@ -359,7 +361,7 @@ def run_mbs(a, ws, rank, local):
     tg_pin = torch.from_numpy(np.ascontiguousarray(tg_host.T)).pin_memory().T
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=a.inner_tol, restart=a.restart,
+    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=a.inner_tol, restart=a.restart, fp64_kernel=a.fp64_kernel,
                 max_iter=50000, max_sweeps=12, stream=stream.cuda_stream, mac_path=a.mac)
     ctx = pkg.Context(2, wl.kappa, **opts)
 
@@ -438,7 +440,7 @@ def run_mbs(a, ws, rank, local):
         # The plain FP64 path on this workload needs thousands of FP64 operator
         # applications (~0.83 s each on GB300); time a capped FP64 solve and
         # scale its per-iteration time by the mixed solve's inner iteration count.
-        ctx64 = pkg.Context(2, wl.kappa, precision=pkg.PREC_FP64, tol=a.tol, restart=a.restart,
+        ctx64 = pkg.Context(2, wl.kappa, precision=pkg.PREC_FP64, tol=a.tol, restart=a.restart, fp64_kernel=a.fp64_kernel,
                             max_iter=a.fp64_iters, stream=stream.cuda_stream)
         ctx64.build_scattering_matrices(wl)
         b64 = ctx64.rhs(v_dev)
@@ -505,6 +507,7 @@ def run_mbs(a, ws, rank, local):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "pairs_per_matvec": pairs_mv, "nrhs": nrhs,
                        "field_targets": M, "restart": a.restart, "inner_tol": a.inner_tol,
+                       "fp64_kernel": "double-float on the FP32 pipe" if a.fp64_kernel else "FP64 pipe",
                        "l2": "256 MiB buffer written before every step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(1, e_steps),
