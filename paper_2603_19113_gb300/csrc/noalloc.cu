@@ -92,7 +92,8 @@ extern "C" mbs_status mbs_apply_G_noalloc(int dim, double kappa, int64_t N, int 
                                           void* stream) {
     if ((dim != 2 && dim != 3) || !(kappa > 0) || N < 0 || T < 1 || nrhs < 1) return MBS_ERR_ARG;
     const size_t cap = (NOALLOC_BYTES - SPLIT_BYTES) / sizeof(double2);
-    if ((size_t)N * (size_t)nrhs > cap) return MBS_ERR_ARG;  // beyond the static scratch
+    // beyond the static scratch; compared without forming N * nrhs, which could wrap
+    if ((uint64_t)N > cap || (size_t)nrhs > cap / (size_t)std::max<int64_t>(N, 1)) return MBS_ERR_ARG;
     if (N == 0) return MBS_OK;
     if (!on_device(body_offsets) || !on_device(body) || !on_device(xw) || !on_device(q) ||
         !on_device(y))

@@ -63,3 +63,7 @@ def test_noalloc_rejects_sizes_beyond_the_static_scratch(env):
     # N * nrhs above the 64 MiB limit: rejected before anything is launched
     st = lib.mbs_apply_G_noalloc(2, 1.0, 4_000_000, 1, p, p, p, 2, p, p, None)
     assert st == 1
+    # sizes whose product wraps around 64 bits (N = 2^40, nrhs = 2^24) are
+    # rejected too, before any pointer is looked at
+    st = lib.mbs_apply_G_noalloc(2, 1.0, 1 << 40, 1, p, p, p, 1 << 24, p, p, None)
+    assert st == 1
