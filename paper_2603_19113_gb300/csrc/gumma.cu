@@ -10,24 +10,26 @@
 // the right-hand sides is a dense product that runs on the tensor cores:
 //   - a CTA owns 128 consecutive targets, one per thread, i.e. one lane of
 //     tensor memory each (the M = 128 rows of the MMA);
-//   - sources are taken in chunks of 8 (never straddling a body); per chunk
-//     each thread writes its 8 phi values into tensor memory as the row of A,
-//     [Re phi_0, Im phi_0, Re phi_1, ...] (K = 16), with A = A_hi + A_lo the
+//   - sources are taken in chunks of 16 (never straddling a body); per chunk
+//     each thread writes its 16 phi values into tensor memory as the row of A,
+//     [Re phi_0, Im phi_0, Re phi_1, ...] (K = 32), with A = A_hi + A_lo the
 //     3xTF32 split (A_hi = A with the low 13 mantissa bits cleared);
-//   - B (K = 16 x N = 2 NR) holds, per source j and right-hand side r,
+//   - B (K = 32 x N = 2 NR) holds, per source j and right-hand side r,
 //         row 2j:   [ Re q_jr | Im q_jr ],   row 2j+1: [ -Im q_jr | Re q_jr ],
 //     so that D[:, r] = Re(phi q) and D[:, NR + r] = Im(phi q); B_hi and B_lo
 //     are prepared once per matvec by g_umma_pack_kernel in the K-major
 //     core-matrix layout of the tensor cores and streamed into a ring of
 //     shared-memory stages by bulk copies (cp.async.bulk + mbarrier);
-//   - one thread issues D += A_hi B_hi + A_hi B_lo + A_lo B_hi (six
-//     kind::tf32 MMAs, K = 8 each) and commits them to an mbarrier; A is
-//     double-buffered in tensor memory so the next chunk's phi evaluation
-//     overlaps the MMAs;
-//   - D is accumulated per source body (a "segment") in one of two tensor-
-//     memory buffers; after a segment's MMAs complete every thread adds its
-//     row of D into FP32 registers, so the tensor-core accumulation never
-//     runs over more than one body's sources.
+//   - one thread of the producer warp issues D += A_hi B_hi + A_hi B_lo +
+//     A_lo B_hi (twelve kind::tf32 MMAs, K = 8 each) per chunk and commits
+//     them to an mbarrier; the phi warps and the producer synchronise only
+//     through mbarriers;
+//   - A and D are single-buffered in tensor memory: a phi warp evaluates the
+//     first half of the next chunk, then waits for the previous chunk's MMAs
+//     before it overwrites A; D accumulates one source body (a "segment") at a
+//     time, and when a body ends every thread adds its row of D into FP32
+//     registers before it signals the next chunk, whose first MMA resets D,
+//     so the tensor-core accumulation never runs over more than one body.
 // Every wait is bounded (about 2 s): on a timeout the kernel sets *err, writes
 // NaN to its outputs, waits (bounded) for its work in flight, frees its tensor
 // memory and returns.
