@@ -82,9 +82,13 @@ typedef struct mbs_options {
                             0: heuristic shape */
     int cuda_graphs;     /* 1 (default): after one direct step, the device work of each block-GMRES step is
                             captured once per context and step index and replayed as a CUDA graph; 0: launch directly */
-    int fp64_kernel;     /* FP64-accurate G_hat (FP64 solves, refinement residuals, apply calls): 0 (default)
-                            on the FP64 pipe; 1 in double-float arithmetic on the FP32 pipe, with FP64 work only
-                            per body pair (agrees with 0 to ~1e-13 relative; not yet timed) */
+    int fp64_kernel;     /* FP64-accurate G_hat (FP64 solves, refinement residuals, apply calls):
+                            0 on the FP64 pipe; 1 in double-float arithmetic on the FP32 pipe, with FP64
+                            work only per body pair (3.4x faster than 0 on GB300 at N = 64,000, 8 RHS;
+                            ~1e-13 relative instead of ~1e-16); 2 (default) automatic: inside solves
+                            double-float when 1e-14 ||S||_F (the FP64 residual floor it leaves, with the
+                            root mean square of ||S_tau||_F over the bodies) is at most tol / 10, else
+                            the FP64 pipe; apply calls use the FP64 pipe */
 } mbs_options;
 
 typedef struct mbs_shape {
@@ -115,13 +119,15 @@ typedef struct mbs_solve_info {
                              and FP64 GMRES, warm-started from the refined iterate, finished */
     double rel_residual;  /* max over RHS of the final FP64 relative residual */
     double seconds;       /* wall time of the call */
+    int fp64_kernel;      /* FP64-accurate G_hat the solve used: 0 FP64 pipe, 1 double-float */
 } mbs_solve_info;
 
 typedef struct mbs_ctx mbs_ctx;
 
 /* Fill *opt with defaults: FP64, tol 1e-11, inner_tol 1e-6, restart 60,
  * max_iter 20000, max_sweeps 8, ls_rcond 1e-14, stream NULL, no budget,
- * automatic G_hat kernel, autotuning and CUDA graphs on, FP64 G_hat on the FP64 pipe. */
+ * automatic G_hat kernel, autotuning and CUDA graphs on, automatic choice of the
+ * FP64-accurate G_hat (fp64_kernel 2). */
 void mbs_default_options(mbs_options* opt);
 
 /* Create a context for dimension dim (2 or 3) and wavenumber kappa > 0
@@ -145,6 +151,11 @@ const char* mbs_last_error(const mbs_ctx* ctx);
  * B ~ B(:, I_hat) Z* (eq. B_fac); A(i,j) = phi(x_i - y_j) (m x n) and
  * D(i,j) = phi(z_i - y_j) (p x n) give the local solve A^+ and the translation
  * C with B C = D; S = Z* C A^+ U with U = (Z*)^T (eq. scattering-matrix).
+ * A^+ is the truncated-SVD pseudo-inverse (singular values above ls_rcond
+ * times the largest; pivoted QR, then one-sided Jacobi on the triangular
+ * factor), C the minimum-norm least-squares solution on the rank of the
+ * pivoted QR of B truncated at ls_rcond (complete orthogonal decomposition;
+ * Sec. 3.1 "truncated SVD or QR", Sec. 4.4 "stabilized").
  * Bodies are rigid placements of shapes (S is reused per shape, Sec. 5.1
  * Example 4).  All of it runs on the device in FP64.
  * Errors: MBS_ERR_ARG (n >= m, k > min(m,p), NaN, bad shape index),
@@ -165,6 +176,16 @@ mbs_status mbs_get_layout(mbs_ctx* ctx, int64_t* N, int64_t* body_offsets, doubl
  * its largest initial column norm when the QR stopped). */
 mbs_status mbs_get_shape(mbs_ctx* ctx, int shape, int* k, int* skel, double* S,
                          double* eps_achieved);
+
+/* Figures of one shape's build (Sec. 3.1, 4.3-4.4; all outputs nullable):
+ * *rank_b = steps of the pivoted QR of B (the rank on which C is the
+ * minimum-norm solution), *rank_a_qr = steps of the pivoted QR of A ahead of
+ * its SVD, *rank_a = singular values of A kept (above ls_rcond times the
+ * largest; the rank of A^+), *sweeps = one-sided Jacobi sweeps that computed
+ * the SVD, *s_norm = Frobenius norm of S.  MBS_ERR_STATE for a shape holding
+ * injected data. */
+mbs_status mbs_get_shape_stats(mbs_ctx* ctx, int shape, int* rank_b, int* rank_a_qr, int* rank_a,
+                               int* sweeps, double* s_norm);
 
 /*
  * Right-hand side b = S v_hat, evaluated as Z* C A^+ v from the boundary data

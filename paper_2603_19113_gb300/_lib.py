@@ -44,6 +44,7 @@ class mbs_solve_info(C.Structure):
         ("matvecs_fp64", C.c_int), ("converged", C.c_int), ("fp64_finish", C.c_int),
         ("rel_residual", C.c_double),
         ("seconds", C.c_double),
+        ("fp64_kernel", C.c_int),
     ]
 
 
@@ -75,6 +76,7 @@ SIGNATURES = {
                                                 C.POINTER(mbs_body)]),
     "mbs_get_layout": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P]),
     "mbs_get_shape": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _P, _D]),
+    "mbs_get_shape_stats": (C.c_int, [_P, C.c_int] + [C.POINTER(C.c_int)] * 4 + [_D]),
     "mbs_rhs": (C.c_int, [_P, C.c_int, _P, _P]),
     "mbs_apply_operator": (C.c_int, [_P, C.c_int, _P, _P]),
     "mbs_apply_G": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),

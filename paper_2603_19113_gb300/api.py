@@ -198,6 +198,17 @@ class Context:
                                          C.c_void_p(S.ctypes.data), C.byref(eps)))
         return {"k": k.value, "skel": skel.astype(np.int64), "S": np.array(S), "eps": eps.value}
 
+    def get_shape_stats(self, shape: int):
+        """Figures of one shape's build: rank_b (pivoted QR of B), rank_a_qr
+        (pivoted QR of A), rank_a (singular values of A kept), the Jacobi
+        sweeps of the SVD and s_norm (Frobenius norm of S)."""
+        v = [C.c_int() for _ in range(4)]
+        sn = C.c_double()
+        self._check(_lib().mbs_get_shape_stats(self._h, shape, *[C.byref(x) for x in v], C.byref(sn)))
+        out = dict(zip(("rank_b", "rank_a_qr", "rank_a", "sweeps"), (x.value for x in v)))
+        out["s_norm"] = sn.value
+        return out
+
     def rhs(self, v):
         a = _Arg(v, self.Mtot)
         out, p = _out_like(a, self.N)

@@ -26,6 +26,10 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # single-precision G_hat kernels: flush denormals, approximate division / square
 # root (these flags touch FP32 arithmetic only; the FP64 kernels are unaffected)
 EXTRA = {f: ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"] for f in ("gmatvec.cu", "gumma.cu")}
+# double-float kernel: no contraction of a separate multiply and add into a
+# fused multiply-add, which would break the exact error terms of the two-sum
+# and two-product transformations (explicit fmaf / fma calls stay fused)
+EXTRA["gdf.cu"] = ["-fmad=false"]
 
 
 def _nvcc() -> str:

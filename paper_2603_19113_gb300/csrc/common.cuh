@@ -97,8 +97,15 @@ void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, do
                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // FP64-accurate G_hat in double-float arithmetic on the FP32 pipe (gdf.cu);
 // d_centres: [T][3] body centres (FP64).  Selected by mbs_options.fp64_kernel = 1.
+// ev0/ev1 as for launch_G_f64: around the kernel passes, not the reduction.
 void launch_G_df(const GLayout& L, const double* d_centres, double kappa, int nrhs, const double2* q,
-                 double2* y, double2* part, int nsplit, const int* d_split_body, cudaStream_t st);
+                 double2* y, double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
+                 cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+// y = sum over the nsplit partial sums part[s * len + e], in split order
+// (deterministic); shared by the FP64-accurate G_hat kernels.
+void launch_reduce_splits64(const double2* part, int nsplit, int64_t len, double2* y, cudaStream_t st);
+// Event record that works inside and outside stream capture.
+void record_event(cudaEvent_t e, cudaStream_t st);
 // tbody (nullable): per target a body whose skeleton sources are left out (-1: none).
 void launch_field_f64(const GLayout& L, double kappa, int64_t M, const double* tgt, int nrhs,
                       const double2* q, double2* u, double2* part, int nsplit,

@@ -44,9 +44,10 @@ __constant__ DfTab<MBS_F64_X4_DEG + 1> c_df4F = df_tab(k4F), c_df4G = df_tab(k4G
 
 constexpr int DF_TPB = 128;  // targets per CTA, one per thread
 constexpr int DF_SB = 64;    // sources staged in shared memory per round (<= DF_TPB)
-constexpr int DF_NR = 8;     // right-hand sides per pass
 
-template <int DIM>
+// NR right-hand sides per pass (4, 8 or 16): phi is evaluated once per pair
+// and pass, so the pass width follows the number of right-hand sides
+template <int DIM, int NR>
 __global__ void __launch_bounds__(DF_TPB) g_df_kernel(const int64_t N, const double* __restrict__ xw,
                                                       const int* __restrict__ body,
                                                       const int64_t* __restrict__ off,
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(DF_TPB) g_df_kernel(const int64_t N, const dou
                                                       const int* __restrict__ split_body) {
     __shared__ float s_d[DIM][2][DF_SB];  // source offsets delta_j (hi, lo)
     __shared__ float s_d2[2][DF_SB];      // |delta_j|^2
-    __shared__ float4 s_q[DF_SB][DF_NR];  // q_j: (re hi, re lo, im hi, im lo)
+    __shared__ float4 s_q[DF_SB][NR];     // q_j: (re hi, re lo, im hi, im lo)
     const DfFit fits[3] = {
         DfFit{(float)MBS_F64_X64_XA, MBS_F64_X64_DEG, c_df64F.hi, c_df64F.lo, c_df64G.hi, c_df64G.lo},
         DfFit{(float)MBS_F64_X16_XA, MBS_F64_X16_DEG, c_df16F.hi, c_df16F.lo, c_df16G.hi, c_df16G.lo},
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(DF_TPB) g_df_kernel(const int64_t N, const dou
             di[a] = df_from_double(xw[(int64_t)a * N + i] - ci[a]);
         }
     const dfl kd = df_from_double(kappa);
-    DfAcc ar[DF_NR], ai[DF_NR];
+    DfAcc ar[NR], ai[NR];
 #pragma unroll
-    for (int r = 0; r < DF_NR; ++r) ar[r] = ai[r] = DfAcc{0.f, 0.f};
+    for (int r = 0; r < NR; ++r) ar[r] = ai[r] = DfAcc{0.f, 0.f};
     const int sb0 = split_body[blockIdx.y], sb1 = split_body[blockIdx.y + 1];
     for (int sb = sb0; sb < sb1; ++sb) {
         const bool act = valid && tb != sb;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(DF_TPB) g_df_kernel(const int64_t N, const dou
                 s_d2[0][tid] = dj2.hi;
                 s_d2[1][tid] = dj2.lo;
 #pragma unroll
-                for (int r = 0; r < DF_NR; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     const double2 qq = (r0 + r < nrhs) ? q[(int64_t)(r0 + r) * N + j] : make_double2(0.0, 0.0);
                     const dfl qr = df_from_double(qq.x), qi = df_from_double(qq.y);
                     s_q[tid][r] = make_float4(qr.hi, qr.lo, qi.hi, qi.lo);
@@ -132,19 +133,19 @@ __global__ void __launch_bounds__(DF_TPB) g_df_kernel(const int64_t N, const dou
                     pim = df_from_double(p.y);
                 }
 #pragma unroll
-                for (int r = 0; r < DF_NR; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     const float4 qq = s_q[jj][r];
                     df_cmac(ar[r], ai[r], pr, pim, dfl{qq.x, qq.y}, dfl{qq.z, qq.w});
                 }
                 if ((jj & 15) == 15)
 #pragma unroll
-                    for (int r = 0; r < DF_NR; ++r) {
+                    for (int r = 0; r < NR; ++r) {
                         df_acc_norm(ar[r]);
                         df_acc_norm(ai[r]);
                     }
             }
 #pragma unroll
-            for (int r = 0; r < DF_NR; ++r) {
+            for (int r = 0; r < NR; ++r) {
                 df_acc_norm(ar[r]);
                 df_acc_norm(ai[r]);
             }
@@ -153,42 +154,51 @@ __global__ void __launch_bounds__(DF_TPB) g_df_kernel(const int64_t N, const dou
     if (!valid) return;
     double2* out = part + (int64_t)blockIdx.y * nrhs * N;
 #pragma unroll
-    for (int r = 0; r < DF_NR; ++r)
+    for (int r = 0; r < NR; ++r)
         if (r0 + r < nrhs)
             out[(int64_t)(r0 + r) * N + i] =
                 make_double2((double)ar[r].hi + (double)ar[r].lo, (double)ai[r].hi + (double)ai[r].lo);
 }
 
-// y = sum of the split partial sums in split order
-__global__ void df_reduce_kernel(const double2* __restrict__ part, int nsplit, int64_t len,
-                                 double2* __restrict__ y) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= len) return;
-    double2 s = part[e];
-    for (int k = 1; k < nsplit; ++k) {
-        const double2 v = part[(int64_t)k * len + e];
-        s.x += v.x;
-        s.y += v.y;
+template <int DIM, int NR>
+void launch_df_pass(const GLayout& L, const double* d_centres, double kappa, int nrhs, int r0,
+                    const double2* q, double2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+    const dim3 grid((unsigned)((L.N + DF_TPB - 1) / DF_TPB), (unsigned)nsplit);
+    g_df_kernel<DIM, NR><<<grid, DF_TPB, 0, st>>>(L.N, L.xw64, L.body, L.off, d_centres, kappa, nrhs, r0,
+                                                  q, part, d_split_body);
+    MBS_CHECK_LAUNCH();
+}
+
+template <int DIM>
+void launch_df_dim(const GLayout& L, const double* d_centres, double kappa, int nrhs, const double2* q,
+                   double2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+    int r0 = 0;
+    while (r0 < nrhs) {
+        const int left = nrhs - r0;
+        if (left <= 4) {
+            launch_df_pass<DIM, 4>(L, d_centres, kappa, nrhs, r0, q, part, nsplit, d_split_body, st);
+            r0 += 4;
+        } else if (left <= 8) {
+            launch_df_pass<DIM, 8>(L, d_centres, kappa, nrhs, r0, q, part, nsplit, d_split_body, st);
+            r0 += 8;
+        } else {
+            launch_df_pass<DIM, 16>(L, d_centres, kappa, nrhs, r0, q, part, nsplit, d_split_body, st);
+            r0 += 16;
+        }
     }
-    y[e] = s;
 }
 
 }  // namespace
 
 void launch_G_df(const GLayout& L, const double* d_centres, double kappa, int nrhs, const double2* q,
-                 double2* y, double2* part, int nsplit, const int* d_split_body, cudaStream_t st) {
+                 double2* y, double2* part, int nsplit, const int* d_split_body, cudaStream_t st,
+                 cudaEvent_t ev0, cudaEvent_t ev1) {
     if (L.N == 0 || nrhs == 0) return;
-    const dim3 grid((unsigned)((L.N + DF_TPB - 1) / DF_TPB), (unsigned)nsplit);
-    for (int r0 = 0; r0 < nrhs; r0 += DF_NR) {
-        if (L.dim == 2)
-            g_df_kernel<2><<<grid, DF_TPB, 0, st>>>(L.N, L.xw64, L.body, L.off, d_centres, kappa, nrhs, r0,
-                                                    q, part, d_split_body);
-        else
-            g_df_kernel<3><<<grid, DF_TPB, 0, st>>>(L.N, L.xw64, L.body, L.off, d_centres, kappa, nrhs, r0,
-                                                    q, part, d_split_body);
-        MBS_CHECK_LAUNCH();
-    }
-    const int64_t len = L.N * nrhs;
-    df_reduce_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
-    MBS_CHECK_LAUNCH();
+    if (ev0) record_event(ev0, st);
+    if (L.dim == 2)
+        launch_df_dim<2>(L, d_centres, kappa, nrhs, q, part, nsplit, d_split_body, st);
+    else
+        launch_df_dim<3>(L, d_centres, kappa, nrhs, q, part, nsplit, d_split_body, st);
+    if (ev1) record_event(ev1, st);
+    launch_reduce_splits64(part, nsplit, L.N * nrhs, y, st);
 }

@@ -94,10 +94,18 @@ DF_HD void df_acc_norm(DfAcc& a) {
     a.lo = s.lo;
 }
 
+// a * b as an unnormalised double-float: the high parts' product exactly
+// (fma), the cross terms added to its error; the accumulator's two-sum takes
+// the normalisation, so the product skips its own (4 operations, not 7)
+DF_HD dfl df_mul_acc(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    return {p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)))};
+}
+
 // (re, im) += phi * q for one right-hand side
 DF_HD void df_cmac(DfAcc& re, DfAcc& im, dfl pr, dfl pi, dfl qr, dfl qi) {
-    df_acc_add(re, df_mul(pr, qr));
-    df_acc_add(re, df_neg(df_mul(pi, qi)));
-    df_acc_add(im, df_mul(pr, qi));
-    df_acc_add(im, df_mul(pi, qr));
+    df_acc_add(re, df_mul_acc(pr, qr));
+    df_acc_add(re, df_neg(df_mul_acc(pi, qi)));
+    df_acc_add(im, df_mul_acc(pr, qi));
+    df_acc_add(im, df_mul_acc(pi, qr));
 }

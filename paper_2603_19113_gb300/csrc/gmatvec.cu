@@ -562,6 +562,8 @@ __global__ void mfs_near_kernel(const int64_t M, const double* __restrict__ pts,
     u[(int64_t)r * M + i] = acc;
 }
 
+}  // namespace
+
 // Timing event on st: inside a stream capture it must become an external
 // event-record node of the graph (recorded on every replay); outside a capture
 // the external flag is not allowed.
@@ -573,8 +575,6 @@ void record_event(cudaEvent_t e, cudaStream_t st) {
     else
         MBS_CUDA_TRY(cudaEventRecord(e, st));
 }
-
-}  // namespace
 
 void launch_pair_table(int dim, int T, const double* d_centres, const double* d_brad,
                        double kappa, float4* pair, float* pair_phi0, cudaStream_t st) {
@@ -620,7 +620,10 @@ void launch_G_f64(const GLayout& L, double kappa, int nrhs, const double2* q, do
         launch_f64_dim<3>(L.N, L.xw64, L.body, L.N, L.xw64, L.off, kappa, nrhs, q, part, nsplit,
                           d_split_body, st);
     if (ev1) record_event(ev1, st);
-    const int64_t len = L.N * nrhs;
+    launch_reduce_splits64(part, nsplit, L.N * nrhs, y, st);
+}
+
+void launch_reduce_splits64(const double2* part, int nsplit, int64_t len, double2* y, cudaStream_t st) {
     reduce_splits_kernel<double2><<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, nsplit, len, y);
     MBS_CHECK_LAUNCH();
 }

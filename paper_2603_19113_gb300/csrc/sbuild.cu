@@ -13,19 +13,30 @@
 //            most eps times the largest initial one; the factorisation goes on
 //            to the numerical rank r_B (relative ls_rcond) for the
 //            least-squares solve below.
-//  phase 2   Z* = [I_k | R11^{-1} R12] in pivot order (ID, eq. B_fac),
-//            C = basic least-squares solution of B C = D from the same
-//            factorisation truncated at r_B (Sec. 4.4),
-//            U = (Z*)^T (Sec. 4.2), pivoted QR of A truncated at r_A with the
-//            reflectors applied to U, and
-//            S = ((Z* C) P_A)(:, 1:r_A) R_A11^{-1} (Q_A^H U)(1:r_A, :),
-//            i.e. S = Z* C A^+ U (eq. scattering-matrix) with A^+ applied as a
-//            truncated pivoted-QR solve.  The division by the small pivots acts
-//            on rows of Z* C before the product with the projections of U, which
-//            keeps the rounding of the ill-conditioned MFS solve out of S.
+//  phase 2   Z* = [I_k | R11^{-1} R12] in pivot order (ID, eq. B_fac);
+//            C = minimum-norm least-squares solution of B C = D on the rank r_B
+//            of that factorisation (Sec. 4.4): a complete orthogonal
+//            decomposition R_B = Rz^H Zq^H from the QR of R_B^H, then
+//            C P_B = Zq Rz^{-H} (Q_B^H D)(1:r_B, :);
+//            U = (Z*)^T (Sec. 4.2) and the pivoted QR of A with its reflectors
+//            applied to U, run to the rounding level (0.01 ls_rcond).
+//  phase 3   truncated SVD of A (Sec. 3.1, "truncated SVD"): one-sided Jacobi
+//            (Hestenes) on X = R_A^H, the columns of X J mutually orthogonal,
+//            so R_A = J Sigma V^H with V = (X J) Sigma^{-1} and
+//            A P_A = (Q_A J) Sigma V^H.  Singular values at most ls_rcond times
+//            the largest are dropped, as in the oracle, so that
+//            A^+ = P_A V_r Sigma_r^{-1} J_r^H Q_A^H, and
+//            S = (Z* C P_A V_r Sigma_r^{-1}) (J_r^H (Q_A^H U)(1:r_A, :))
+//            (eq. scattering-matrix).  The division by the small singular
+//            values acts on the columns of Z* C P_A V_r before the product with
+//            the projections of U, which keeps the rounding of the
+//            ill-conditioned MFS solve out of S.  Pivoted QR ahead of the
+//            Jacobi sweeps (Drmac & Veselic 2008) leaves X with strongly graded
+//            columns, so few sweeps converge.
 //
 // The right-hand side b = Z* C A^+ v (Sec. 4.5) is formed right to left from
-// the stored factors (rhs_kernel): Q_A^H v, a triangular solve, C, then Z*.
+// the stored factors (rhs_kernel): Q_A^H v, J_r^H, the scaled right singular
+// vectors, C, then Z*.
 #include <algorithm>
 
 #include "bessel.cuh"
@@ -123,6 +134,160 @@ __device__ void fill_kernel_matrix(double2* M, int ld, const double* T, int nt, 
     }
 }
 
+// Step j of a Householder QR of A (rows x ncols columns, leading dimension
+// ld): the unit reflector v of column j (rows j..rows-1) replaces the column
+// there (H = I - 2 v v^H), diag[j] = R_jj, and H is applied to columns
+// j+1 .. ntot-1 (one warp per column).  With nrm2 given, the squared norms of
+// rows j+1.. of columns j+1 .. ncols-1 are refreshed in full.
+__device__ void householder_step(double2* A, int ld, int rows, int j, int ncols, int ntot,
+                                 double2* diag, double* nrm2, double2* s_v, Red& red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double2* cj = A + (int64_t)j * ld;
+    double sl = 0.0;
+    for (int i = j + threadIdx.x; i < rows; i += blockDim.x) sl += cabs2(cj[i]);
+    const double nx2 = block_sum(sl, red);
+    const double2 x0 = cj[j];
+    const double ax0 = sqrt(cabs2(x0));
+    const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    const double nx = sqrt(nx2);
+    const double2 alpha = make_double2(-ph.x * nx, -ph.y * nx);
+    const double2 v0 = csub(x0, alpha);
+    const double nv2 = nx2 - ax0 * ax0 + cabs2(v0);
+    const double inv = nv2 > 0.0 ? 1.0 / sqrt(nv2) : 0.0;
+    __syncthreads();
+    for (int i = j + threadIdx.x; i < rows; i += blockDim.x) {
+        const double2 v = (i == j) ? cscale(v0, inv) : cscale(cj[i], inv);
+        s_v[i - j] = v;
+        cj[i] = v;
+    }
+    if (threadIdx.x == 0) diag[j] = alpha;
+    __syncthreads();
+    for (int c = j + 1 + w; c < ntot; c += NW) {
+        double2* cc = A + (int64_t)c * ld;
+        double2 d = make_double2(0.0, 0.0);
+        for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(s_v[i - j], cc[i]));
+        d = warp_sum2(d);
+        d = cscale(d, 2.0);
+        double s = 0.0;
+        for (int i = j + lane; i < rows; i += 32) {
+            const double2 nv = csub(cc[i], cmul(s_v[i - j], d));
+            cc[i] = nv;
+            if (i > j) s += cabs2(nv);
+        }
+        if (nrm2 && c < ncols) {
+            s = warp_sum(s);
+            if (lane == 0) nrm2[c] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Unpivoted Householder QR of the rows x cols matrix A (leading dimension ld),
+// same storage as householder_step: reflectors on and below the diagonal,
+// R above it and its diagonal in diag.
+__device__ void cta_qr(double2* A, int ld, int rows, int cols, double2* diag, double2* s_v,
+                       Red& red) {
+    const int kmax = min(rows, cols);
+    for (int j = 0; j < kmax; ++j) householder_step(A, ld, rows, j, cols, cols, diag, nullptr, s_v, red);
+}
+
+// X <- H_0 H_1 ... H_{nref-1} X for the reflectors stored in the columns of V
+// (v_j in rows j..rows-1 of column j, leading dimension ldv): the orthogonal
+// factor of a QR applied to the rows x ncols matrix X (leading dimension ldx).
+__device__ void cta_apply_q(const double2* V, int ldv, int rows, int nref, double2* X, int ldx,
+                            int ncols) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = nref - 1; j >= 0; --j) {
+        const double2* vj = V + (int64_t)j * ldv;
+        for (int c = w; c < ncols; c += NW) {
+            double2* xc = X + (int64_t)c * ldx;
+            double2 d = make_double2(0.0, 0.0);
+            for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(vj[i], xc[i]));
+            d = cscale(warp_sum2(d), 2.0);
+            for (int i = j + lane; i < rows; i += 32) xc[i] = csub(xc[i], cmul(vj[i], d));
+        }
+        __syncthreads();
+    }
+}
+
+// One-sided Jacobi (Hestenes 1958) on the r columns of X (rows x r, leading
+// dimension ldx): plane rotations from the right until every pair of columns
+// is orthogonal to tol relative to the product of their norms; X J = W with
+// orthogonal columns, J (r x r, leading dimension ldj, starts as I)
+// accumulating the rotations.  Pairs are taken in round-robin tournament
+// order, so every round rotates r/2 disjoint pairs, one warp per pair; the
+// result does not depend on the warp schedule.  Returns the sweeps run
+// (maxsweep + 1 if the last one still rotated).
+__device__ int cta_jacobi(double2* X, int ldx, int rows, int r, double2* Jm, int ldj, double tol,
+                          int maxsweep, int* s_flag) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int re = r + (r & 1);  // with a dummy column when r is odd
+    const int half = re / 2;
+    for (int sweep = 0; sweep < maxsweep; ++sweep) {
+        if (threadIdx.x == 0) *s_flag = 0;
+        __syncthreads();
+        for (int rho = 0; rho < re - 1; ++rho) {
+            for (int pi = w; pi < half; pi += NW) {
+                int i, j;
+                if (pi == 0) {
+                    i = rho;
+                    j = re - 1;
+                } else {
+                    i = (rho + pi) % (re - 1);
+                    j = (rho - pi + re - 1) % (re - 1);
+                }
+                if (i > j) {
+                    const int t = i;
+                    i = j;
+                    j = t;
+                }
+                if (j >= r) continue;
+                double2* xi = X + (int64_t)i * ldx;
+                double2* xj = X + (int64_t)j * ldx;
+                double a = 0.0, b = 0.0;
+                double2 c = make_double2(0.0, 0.0);
+                for (int l = lane; l < rows; l += 32) {
+                    const double2 u = xi[l], v = xj[l];
+                    a += cabs2(u);
+                    b += cabs2(v);
+                    c = cadd(c, cmulc(u, v));
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                c = warp_sum2(c);
+                const double ac = sqrt(cabs2(c));
+                if (!(ac > 0.0) || ac <= tol * sqrt(a) * sqrt(b)) continue;
+                if (lane == 0) *s_flag = 1;
+                // x_j' = e^{-i arg c} x_j makes the pair's inner product real and
+                // positive; then the real rotation with t = tan(theta) the
+                // smaller root of t^2 + 2 zeta t - 1 = 0
+                const double2 ph = make_double2(c.x / ac, -c.y / ac);
+                const double zeta = (b - a) / (2.0 * ac);
+                const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+                const double cs = 1.0 / hypot(1.0, t);
+                const double sn = cs * t;
+                for (int l = lane; l < rows; l += 32) {
+                    const double2 u = xi[l], v = cmul(ph, xj[l]);
+                    xi[l] = make_double2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+                    xj[l] = make_double2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+                }
+                double2* ji = Jm + (int64_t)i * ldj;
+                double2* jj = Jm + (int64_t)j * ldj;
+                for (int l = lane; l < r; l += 32) {
+                    const double2 u = ji[l], v = cmul(ph, jj[l]);
+                    ji[l] = make_double2(cs * u.x - sn * v.x, cs * u.y - sn * v.y);
+                    jj[l] = make_double2(sn * u.x + cs * v.x, sn * u.y + cs * v.y);
+                }
+            }
+            __syncthreads();
+        }
+        const int more = *s_flag;
+        __syncthreads();
+        if (!more) return sweep + 1;
+    }
+    return maxsweep + 1;
+}
+
 // Pivoted Householder QR of the first `cols` columns of A (rows x cols,
 // leading dimension ld); `extra` further columns are transformed by the same
 // reflectors but never pivoted.  Column j of the result holds the unit
@@ -192,46 +357,7 @@ __device__ void cta_cpqr(double2* A, int ld, int rows, int cols, int extra, int*
             }
         }
         __syncthreads();
-        // Householder reflector of column j, rows j..rows-1
-        double2* cj = A + (int64_t)j * ld;
-        double sl = 0.0;
-        for (int i = j + threadIdx.x; i < rows; i += blockDim.x) sl += cabs2(cj[i]);
-        const double nx2 = block_sum(sl, red);
-        const double2 x0 = cj[j];
-        const double ax0 = sqrt(cabs2(x0));
-        const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-        const double nx = sqrt(nx2);
-        const double2 alpha = make_double2(-ph.x * nx, -ph.y * nx);
-        const double2 v0 = csub(x0, alpha);
-        const double nv2 = nx2 - ax0 * ax0 + cabs2(v0);
-        const double inv = nv2 > 0.0 ? 1.0 / sqrt(nv2) : 0.0;
-        __syncthreads();
-        for (int i = j + threadIdx.x; i < rows; i += blockDim.x) {
-            const double2 v = (i == j) ? cscale(v0, inv) : cscale(cj[i], inv);
-            s_v[i - j] = v;
-            cj[i] = v;
-        }
-        if (threadIdx.x == 0) diag[j] = alpha;
-        __syncthreads();
-        // apply H_j to the trailing columns (warp per column), refresh norms
-        for (int c = j + 1 + w; c < cols + extra; c += NW) {
-            double2* cc = A + (int64_t)c * ld;
-            double2 d = make_double2(0.0, 0.0);
-            for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(s_v[i - j], cc[i]));
-            d = warp_sum2(d);
-            d = cscale(d, 2.0);
-            double s = 0.0;
-            for (int i = j + lane; i < rows; i += 32) {
-                const double2 nv = csub(cc[i], cmul(s_v[i - j], d));
-                cc[i] = nv;
-                if (i > j) s += cabs2(nv);
-            }
-            if (c < cols) {
-                s = warp_sum(s);
-                if (lane == 0) nrm2[c] = s;
-            }
-        }
-        __syncthreads();
+        householder_step(A, ld, rows, j, cols, cols + extra, diag, nrm2, s_v, red);
     }
     if (kskel < 0) {
         kskel = (kfix > 0) ? min(kfix, j) : j;
@@ -282,7 +408,7 @@ __global__ void __launch_bounds__(SBT) sbuild_phase1(SBuildJob* jobs, double kap
 }
 
 // ----------------------------------------------------------------------------
-// phase 2: Z*, C, U, pivoted QR of A (with U), S
+// phase 2: Z*, C (minimum norm), U, pivoted QR of A (with U)
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(SBT) sbuild_phase2(SBuildJob* jobs, double rcond) {
     __shared__ Red red;
@@ -302,13 +428,42 @@ __global__ void __launch_bounds__(SBT) sbuild_phase2(SBuildJob* jobs, double rco
         const int i = (int)(e % k), c = (int)(e / k);
         J.Zs[(int64_t)J.permB[k + c] * k + i] = J.W1[e];
     }
-    // C (m x n, ld m): R_B(0:rB,0:rB)^{-1} (Q^H D)(0:rB, :) in pivot order, zeros beyond rB
-    cta_backsub(J.BD, p, J.diagB, rB, J.BD + (int64_t)m * p, p, n, J.W2, rB > 0 ? rB : 1);
-    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) J.C[e] = make_double2(0.0, 0.0);
+    // C (m x n, ld m): minimum-norm solution of R_B(0:rB, :) (C P_B) = (Q_B^H D)(0:rB, :).
+    // X_B = R_B^H (m x rB, ld m), then X_B = Zq Rz (unpivoted QR), so that
+    // R_B = Rz^H Zq^H and C P_B = Zq Rz^{-H} (Q_B^H D)(0:rB, :).
+    for (int64_t e = threadIdx.x; e < (int64_t)m * rB; e += blockDim.x) {
+        const int c = (int)(e % m), i = (int)(e / m);
+        double2 v = make_double2(0.0, 0.0);
+        if (c == i)
+            v = J.diagB[i];
+        else if (c > i)
+            v = J.BD[(int64_t)c * p + i];
+        J.XB[e] = make_double2(v.x, -v.y);
+    }
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)rB * n; e += blockDim.x) {
-        const int i = (int)(e % rB), c = (int)(e / rB);
-        J.C[(int64_t)c * m + J.permB[i]] = J.W2[e];
+    cta_qr(J.XB, m, m, rB, J.diagZ, s_v, red);
+    // Y = Rz^{-H} (Q_B^H D)(0:rB, :) by forward substitution (Rz^H is lower
+    // triangular), one thread per column, into W2 (rB x n, ld rB)
+    const int ldy = rB > 0 ? rB : 1;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int i = 0; i < rB; ++i) {
+            double2 sum = J.BD[(int64_t)(m + c) * p + i];
+            for (int l = 0; l < i; ++l)
+                sum = csub(sum, cmulc(J.XB[(int64_t)i * m + l], J.W2[(int64_t)c * ldy + l]));
+            const double2 d = J.diagZ[i];
+            J.W2[(int64_t)c * ldy + i] = cscale(cmul(d, sum), 1.0 / cabs2(d));  // sum / conj(d)
+        }
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+        const int i = (int)(e % m), c = (int)(e / m);
+        J.W3[e] = i < rB ? J.W2[(int64_t)c * ldy + i] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    cta_apply_q(J.XB, m, m, rB, J.W3, m, n);
+    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+        const int i = (int)(e % m), c = (int)(e / m);
+        J.C[(int64_t)c * m + J.permB[i]] = J.W3[e];
     }
     // U = (Z*)^T into AU columns n..n+k-1 (m x k, ld m)
     __syncthreads();
@@ -317,50 +472,127 @@ __global__ void __launch_bounds__(SBT) sbuild_phase2(SBuildJob* jobs, double rco
         J.AU[(int64_t)(n + c) * m + i] = J.Zs[(int64_t)i * k + c];
     }
     __syncthreads();
-    // pivoted QR of A (m x n) truncated at rcond, reflectors applied to U
+    // pivoted QR of A (m x n), reflectors applied to U, run down to the
+    // rounding level: the truncation itself is done on the singular values
+    const double rq = 0.01 * rcond;
     int kdummy;
     double edummy;
-    cta_cpqr(J.AU, m, m, n, k, J.permA, J.diagA, J.nrm2, s_v, -1, rcond, rcond, red, &J.rankA,
-             &kdummy, &edummy);
-    const int rA = J.rankA;
-    // M = Z* C (k x n) with its columns permuted by P_A: MP(:, j) = M(:, permA[j]); into W1
-    for (int64_t e = threadIdx.x; e < (int64_t)k * rA; e += blockDim.x) {
-        const int i = (int)(e % k), j = (int)(e / k);
-        const int col = J.permA[j];
-        double2 s = make_double2(0.0, 0.0);
-        for (int l = 0; l < m; ++l) s = cadd(s, cmul(J.Zs[(int64_t)l * k + i], J.C[(int64_t)col * m + l]));
-        J.W1[e] = s;
+    cta_cpqr(J.AU, m, m, n, k, J.permA, J.diagA, J.nrm2, s_v, -1, rq, rq, red, &J.rankA, &kdummy,
+             &edummy);
+}
+
+// ----------------------------------------------------------------------------
+// phase 3: truncated SVD of A from its pivoted QR (one-sided Jacobi on
+// R_A^H), the factors of A^+, and S
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(SBT) sbuild_phase3(SBuildJob* jobs, double rcond) {
+    __shared__ Red red;
+    __shared__ int s_flag, s_r;
+    SBuildJob& J = jobs[blockIdx.x];
+    const int m = J.m, n = J.n, k = J.k, rA = J.rankA;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // X = R_A^H (n x rA, ld n) and J = I (rA x rA, ld n)
+    for (int64_t e = threadIdx.x; e < (int64_t)n * rA; e += blockDim.x) {
+        const int c = (int)(e % n), i = (int)(e / n);
+        double2 v = make_double2(0.0, 0.0);
+        if (c == i)
+            v = J.diagA[i];
+        else if (c > i)
+            v = J.AU[(int64_t)c * m + i];
+        J.XA[e] = make_double2(v.x, -v.y);
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)rA * rA; e += blockDim.x) {
+        const int l = (int)(e % rA), i = (int)(e / rA);
+        J.JA[(int64_t)i * n + l] = make_double2(l == i ? 1.0 : 0.0, 0.0);
     }
     __syncthreads();
-    // Gc R_A11 = MP  (row-wise forward substitution), in place in W1 (k x rA, ld k)
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        for (int j = 0; j < rA; ++j) {
-            double2 s = J.W1[(int64_t)j * k + i];
-            for (int l = 0; l < j; ++l)
-                s = csub(s, cmul(J.W1[(int64_t)l * k + i], J.AU[(int64_t)j * m + l]));
-            const double2 d = J.diagA[j];
-            J.W1[(int64_t)j * k + i] = cscale(cmulc(d, s), 1.0 / cabs2(d));
-        }
+    const double tol = 2.220446049250313e-16 * sqrt((double)max(n, 1));
+    const int sweeps = cta_jacobi(J.XA, n, n, rA, J.JA, n, tol, 60, &s_flag);
+    // singular values = column norms of X J
+    for (int i = w; i < rA; i += NW) {
+        double sum = 0.0;
+        for (int l = lane; l < n; l += 32) sum += cabs2(J.XA[(int64_t)i * n + l]);
+        sum = warp_sum(sum);
+        if (lane == 0) J.sig[i] = sqrt(sum);
     }
     __syncthreads();
-    // S = Gc (Q_A^H U)(0:rA, :)   (k x k, ld k)
+    double mloc = 0.0;
+    for (int i = threadIdx.x; i < rA; i += blockDim.x) mloc = fmax(mloc, J.sig[i]);
+    const double smax = block_max(mloc, red);
+    if (threadIdx.x == 0) {
+        int r = 0;
+        for (int i = 0; i < rA; ++i)
+            if (J.sig[i] > rcond * smax) J.keep[r++] = i;
+        s_r = r;
+        J.rankS = r;
+        J.sweepsA = sweeps;
+    }
+    __syncthreads();
+    const int r = s_r;
+    // F = P_A V_r Sigma_r^{-1} = P_A (X J)(:, kept) Sigma_r^{-2}  (n x r, ld n, rows in
+    // the original column order of A)
+    for (int64_t e = threadIdx.x; e < (int64_t)n * r; e += blockDim.x) {
+        const int row = (int)(e % n), slot = (int)(e / n);
+        const int i = J.keep[slot];
+        const double sg = J.sig[i];
+        J.FA[(int64_t)slot * n + J.permA[row]] = cscale(J.XA[(int64_t)i * n + row], 1.0 / (sg * sg));
+    }
+    // kept columns of J moved to the front, in order (a source column is never
+    // the destination of an earlier one)
+    for (int slot = 0; slot < r; ++slot) {
+        const int i = J.keep[slot];
+        if (i != slot)
+            for (int l = threadIdx.x; l < rA; l += blockDim.x)
+                J.JA[(int64_t)slot * n + l] = J.JA[(int64_t)i * n + l];
+        __syncthreads();
+    }
+    // M = Z* C (k x n, ld k) into W1
+    for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
+        const int i = (int)(e % k), c = (int)(e / k);
+        double2 sum = make_double2(0.0, 0.0);
+        for (int l = 0; l < m; ++l) sum = cadd(sum, cmul(J.Zs[(int64_t)l * k + i], J.C[(int64_t)c * m + l]));
+        J.W1[e] = sum;
+    }
+    // H = J_r^H (Q_A^H U)(0:rA, :)  (r x k, ld r) into W3
+    const int ldh = r > 0 ? r : 1;
+    for (int64_t e = threadIdx.x; e < (int64_t)r * k; e += blockDim.x) {
+        const int i = (int)(e % ldh), c = (int)(e / ldh);
+        double2 sum = make_double2(0.0, 0.0);
+        for (int l = 0; l < rA; ++l)
+            sum = cadd(sum, cmulc(J.JA[(int64_t)i * n + l], J.AU[(int64_t)(n + c) * m + l]));
+        J.W3[e] = sum;
+    }
+    __syncthreads();
+    // G = M F  (k x r, ld k) into XB
+    for (int64_t e = threadIdx.x; e < (int64_t)k * r; e += blockDim.x) {
+        const int i = (int)(e % k), c = (int)(e / k);
+        double2 sum = make_double2(0.0, 0.0);
+        for (int l = 0; l < n; ++l) sum = cadd(sum, cmul(J.W1[(int64_t)l * k + i], J.FA[(int64_t)c * n + l]));
+        J.XB[e] = sum;
+    }
+    __syncthreads();
+    // S = G H  (k x k, ld k), and its Frobenius norm
+    double sq = 0.0;
     for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
         const int i = (int)(e % k), c = (int)(e / k);
-        double2 s = make_double2(0.0, 0.0);
-        for (int l = 0; l < rA; ++l)
-            s = cadd(s, cmul(J.W1[(int64_t)l * k + i], J.AU[(int64_t)(n + c) * m + l]));
-        J.S[e] = s;
+        double2 sum = make_double2(0.0, 0.0);
+        for (int l = 0; l < r; ++l) sum = cadd(sum, cmul(J.XB[(int64_t)l * k + i], J.W3[(int64_t)c * ldh + l]));
+        J.S[e] = sum;
+        sq += cabs2(sum);
     }
+    sq = block_sum(sq, red);
+    if (threadIdx.x == 0) J.snorm = sqrt(sq);
 }
 
 // ----------------------------------------------------------------------------
 // right-hand side b_tau = Z* C A^+ v_tau, right to left, one CTA per (body, rhs)
 // ----------------------------------------------------------------------------
-// qm = A^+ t for one body with the stored pivoted QR of A truncated at rank
-// r_A (basic solution): t <- Q_A^H t by the Householder reflectors, back
-// substitution with R_A11, and the column permutation.  t (m) and qm (n) are
-// in shared memory; every thread of the block takes part.
-__device__ void apply_Apinv(const RhsBody& B, double2* t, double2* qm, double* rs, double* rs2) {
+// qm = A^+ t for one body from the stored factors of the truncated SVD:
+// t <- Q_A^H t by the Householder reflectors, z = J_r^H t(0:rA) (r values),
+// qm = F z with F = P_A V_r Sigma_r^{-1}.  t (m), z (n) and qm (n) are in
+// shared memory; every thread of the block takes part.
+__device__ void apply_Apinv(const RhsBody& B, double2* t, double2* z, double2* qm, double* rs,
+                            double* rs2) {
     const int m = B.m, n = B.n;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < B.rankA; ++j) {
@@ -383,17 +615,16 @@ __device__ void apply_Apinv(const RhsBody& B, double2* t, double2* qm, double* r
         for (int i = j + threadIdx.x; i < m; i += blockDim.x) t[i] = csub(t[i], cmul(vj[i], tot));
         __syncthreads();
     }
-    // back substitution with R_A11 (thread 0: rA is small) into qm in pivot order
-    for (int i = threadIdx.x; i < n; i += blockDim.x) qm[i] = make_double2(0.0, 0.0);
+    for (int s = threadIdx.x; s < B.rankS; s += blockDim.x) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int l = 0; l < B.rankA; ++l) sum = cadd(sum, cmulc(B.J[(int64_t)s * n + l], t[l]));
+        z[s] = sum;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = B.rankA - 1; i >= 0; --i) {
-            double2 s = t[i];
-            for (int l = i + 1; l < B.rankA; ++l) s = csub(s, cmul(B.A[(int64_t)l * m + i], t[l]));
-            const double2 d = B.diagA[i];
-            t[i] = cscale(cmulc(d, s), 1.0 / cabs2(d));
-        }
-        for (int i = 0; i < B.rankA; ++i) qm[B.permA[i]] = t[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int s = 0; s < B.rankS; ++s) sum = cadd(sum, cmul(B.F[(int64_t)s * n + i], z[s]));
+        qm[i] = sum;
     }
     __syncthreads();
 }
@@ -406,9 +637,10 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsBody* __restrict__ bo
     const int tau = blockIdx.x, r = blockIdx.y;
     const RhsBody B = bodies[tau];
     const int m = B.m, n = B.n, k = B.k;
-    double2* t = sm;          // m
-    double2* qm = sm + m;     // n
-    double2* q = sm + m + n;  // m
+    double2* t = sm;              // m
+    double2* qm = sm + m;         // n
+    double2* q = sm + m + n;      // m
+    double2* z = sm + 2 * m + n;  // n
     const double2* vin = v + (int64_t)r * Mtot + B.voff;
     for (int i = threadIdx.x; i < m; i += blockDim.x) t[i] = vin[i];
     __syncthreads();
@@ -420,7 +652,7 @@ __global__ void __launch_bounds__(256) rhs_kernel(const RhsBody* __restrict__ bo
         }
         return;
     }
-    apply_Apinv(B, t, qm, rs, rs2);
+    apply_Apinv(B, t, z, qm, rs, rs2);
     // q = C q_mfs
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double2 s = make_double2(0.0, 0.0);
@@ -446,8 +678,9 @@ __global__ void __launch_bounds__(256) recon_kernel(const RhsBody* __restrict__ 
     const int tau = blockIdx.x, r = blockIdx.y;
     const RhsBody B = bodies[tau];
     const int m = B.m, n = B.n, k = B.k;
-    double2* t = sm;       // m
-    double2* qm = sm + m;  // n
+    double2* t = sm;           // m
+    double2* qm = sm + m;      // n
+    double2* z = sm + m + n;   // n
     const double2* vin = v + (int64_t)r * Mtot + B.voff;
     const double2* wh = w_hat + (int64_t)r * N + B.boff;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -456,7 +689,7 @@ __global__ void __launch_bounds__(256) recon_kernel(const RhsBody* __restrict__ 
         t[i] = s;
     }
     __syncthreads();
-    apply_Apinv(B, t, qm, rs, rs2);
+    apply_Apinv(B, t, z, qm, rs, rs2);
     for (int j = threadIdx.x; j < n; j += blockDim.x) qmfs[(int64_t)r * Nm + B.moff + j] = qm[j];
 }
 
@@ -484,12 +717,14 @@ void launch_sbuild_phase2(SBuildJob* d_jobs, int njobs, int mmax, double rcond, 
                                           (int)sm));
     sbuild_phase2<<<njobs, SBT, sm, st>>>(d_jobs, rcond);
     MBS_CHECK_LAUNCH();
+    sbuild_phase3<<<njobs, SBT, 0, st>>>(d_jobs, rcond);
+    MBS_CHECK_LAUNCH();
 }
 
 void launch_rhs(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, const double2* v,
                 int64_t Mtot, double2* b, int64_t N, cudaStream_t st) {
     if (T == 0 || nrhs == 0) return;
-    const size_t sm = (size_t)(2 * mmax + nmax) * sizeof(double2);
+    const size_t sm = (size_t)(2 * mmax + 2 * nmax) * sizeof(double2);
     if (sm > 48 * 1024)
         MBS_CUDA_TRY(cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm));
@@ -502,7 +737,7 @@ void launch_recon(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, 
                   int64_t Mtot, const double2* w_hat, int64_t N, double2* qmfs, int64_t Nm,
                   cudaStream_t st) {
     if (T == 0 || nrhs == 0) return;
-    const size_t sm = (size_t)(mmax + nmax) * sizeof(double2);
+    const size_t sm = (size_t)(mmax + 2 * nmax) * sizeof(double2);
     if (sm > 48 * 1024)
         MBS_CUDA_TRY(cudaFuncSetAttribute(recon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm));

@@ -14,18 +14,29 @@ struct SBuildJob {
     double eps;     // else: relative stopping tolerance
     // workspace
     double2* BD;    // p x (m + n), ld p: B | D, factored in place
-    double2* AU;    // m x (n + kcap), ld m: A | U, factored in place (kept: A's reflectors, R_A)
+    double2* AU;    // m x (n + kcap), ld m: A | U, factored in place (kept: A's reflectors)
     double2* W1;    // kcap x max(m, n)
     double2* W2;    // min(p, m) x n
+    double2* W3;    // m x n
+    double2* XB;    // m x min(p, m): R_B^H and its QR
+    double2* diagZ; // min(p, m)
+    double2* XA;    // n x n: R_A^H, rotated by the Jacobi sweeps
+    double* sig;    // n singular values of A
+    int* keep;      // n: columns kept by the truncation
     double* nrm2;   // max(m, n)
     int* permB;     // m
     double2* diagB; // min(p, m)
-    int* permA;     // n (kept)
-    double2* diagA; // n (kept)
+    int* permA;     // n
+    double2* diagA; // n
+    double2* JA;    // n x n (kept): accumulated rotations, kept columns first
+    double2* FA;    // n x n (kept): F = P_A V_r Sigma_r^{-1}, first rankS columns
     // outputs
     int k;          // skeleton count
     int rankB;
-    int rankA;
+    int rankA;      // steps of the pivoted QR of A
+    int rankS;      // singular values of A kept (> ls_rcond * largest)
+    int sweepsA;    // Jacobi sweeps run
+    double snorm;   // Frobenius norm of S
     double eps_ach;
     int* skel;      // kcap
     double2* Zs;    // k x m, ld k (kept)
@@ -34,13 +45,13 @@ struct SBuildJob {
 };
 
 struct RhsBody {
-    int m, n, k, rankA;
+    int m, n, k, rankA, rankS;
     int64_t voff;   // first collocation row of this body in v
     int64_t boff;   // first skeleton row of this body in b
     int64_t moff;   // first MFS source of this body in q_mfs
-    const double2* A;      // reflectors + R_A (m x n, ld m)
-    const double2* diagA;
-    const int* permA;
+    const double2* A;      // Householder reflectors of the pivoted QR of A (m x n, ld m)
+    const double2* J;      // rotations of the truncated SVD of A (ld n, first rankS columns)
+    const double2* F;      // P_A V_r Sigma_r^{-1} (n x rankS, ld n)
     const double2* C;      // m x n
     const double2* Zs;     // k x m
     const double2* W;      // injected k x m, or nullptr

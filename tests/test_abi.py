@@ -54,8 +54,8 @@ def test_default_options_and_argument_errors_without_gpu():
     o.restart = 0
     assert lib.mbs_create(2, 1.0, C.byref(o), C.byref(h)) == 1  # bad restart
     lib.mbs_default_options(C.byref(o))
-    assert o.fp64_kernel == 0 and o.cuda_graphs == 1 and o.inner_tol == 1e-6
-    for field, bad in (("fp64_kernel", 2), ("mac_path", 4), ("inner_tol", 0.0)):
+    assert o.fp64_kernel == 2 and o.cuda_graphs == 1 and o.inner_tol == 1e-6
+    for field, bad in (("fp64_kernel", 3), ("mac_path", 4), ("inner_tol", 0.0)):
         lib.mbs_default_options(C.byref(o))
         setattr(o, field, bad)
         assert lib.mbs_create(2, 1.0, C.byref(o), C.byref(h)) == 1, field

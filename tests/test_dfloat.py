@@ -22,7 +22,7 @@ def lib(tmp_path_factory):
     if gxx is None:
         pytest.skip("g++ not available")
     out = tmp_path_factory.mktemp("dfloat") / "libdfloat_test.so"
-    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", HARNESS, "-o", str(out)],
+    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", "-ffp-contract=off", HARNESS, "-o", str(out)],
                    check=True, capture_output=True)
     L = ctypes.CDLL(str(out))
     for f, t in (("df_eft", ctypes.c_float), ("df_ops", ctypes.c_double)):

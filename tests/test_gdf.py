@@ -27,7 +27,7 @@ def lib(tmp_path_factory):
     if gxx is None:
         pytest.skip("g++ not available")
     out = tmp_path_factory.mktemp("gdf") / "libgdf_test.so"
-    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", HARNESS, "-o", str(out)],
+    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", "-ffp-contract=off", HARNESS, "-o", str(out)],
                    check=True, capture_output=True)
     L = ctypes.CDLL(str(out))
     D, I64 = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)

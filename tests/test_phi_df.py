@@ -25,7 +25,7 @@ def lib(tmp_path_factory):
     if gxx is None:
         pytest.skip("g++ not available")
     out = tmp_path_factory.mktemp("phidf") / "libphidf_test.so"
-    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", HARNESS, "-o", str(out)],
+    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-fno-fast-math", "-ffp-contract=off", HARNESS, "-o", str(out)],
                    check=True, capture_output=True)
     L = ctypes.CDLL(str(out))
     F, I = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)
