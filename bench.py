@@ -12,6 +12,14 @@ phi evaluation with its multiply-add into all 8 right-hand sides; every
 operator application and the field evaluation count).  Under torchrun each
 rank runs an independent replica (the path is not sharded across GPUs).
 
+--config 2 / 3 runs the same measurement on the two largest single-GPU
+workloads (2D, 10,000 bodies, N ~ 700k, 16 waves; 3D, 2000 ellipsoids,
+N = 600,000, 4 waves).  Their solves need thousands of iterations, so one
+step there is the S build, the right-hand side, a capped mixed solve (a fixed
+number of block-GMRES steps and its FP64 residual) and the field; the line
+reports the pair-interaction rate, the kernel roofline and the S-build time,
+not a time to solution.
+
 --impl reference times the CPU oracle (numpy/scipy FP64) on a bounded
 sample of the same workload with the same metric.
 """
@@ -32,12 +40,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Ĝ pair-interactions/s; time-to-1e-9 mixed vs FP64 on GB300; served p50/p99"
 UNIT = "pair-interactions/s"
-WORKLOAD = ("2D sound-soft, 1000 bodies (circle, 3-star, ellipse 1:0.6; radius 1) on a jittered "
-            "32x32 lattice in a 100x100 box, random rotations, kappa=40, m=128 n=64 k=64 p=129 "
-            "per body (N=64,000), 8 plane waves; mixed FP32/FP64-IR solve to rel. residual 1e-11")
-# convention: one pair = one phi (35 flops: FFMA = 2, special function = 1) plus a complex
-# multiply-add (8 flops) into every right-hand side
-FLOPS_PER_PAIR_2D = lambda nrhs: 35 + 8 * nrhs  # noqa: E731
+WORKLOADS = {
+    1: ("2D sound-soft, 1000 bodies (circle, 3-star, ellipse 1:0.6; radius 1) on a jittered "
+        "32x32 lattice in a 100x100 box, random rotations, kappa=40, m=128 n=64 k=64 p=129 "
+        "per body (N=64,000), 8 plane waves; mixed FP32/FP64-IR solve to rel. residual 1e-11"),
+    2: ("2D sound-soft, 10,000 bodies of radius U(0.5,1.5) (circle, 3-star, ellipse) on a jittered "
+        "100x100 lattice in a 400x400 box, kappa=20, k=clamp(3.5 kappa rho, 32, 128), m=2k, n=k, "
+        "p=2k+1 (N=700,230), 16 plane waves; S build of 10,000 unique shapes + capped mixed solve"),
+    3: ("3D sound-soft, 2000 ellipsoids (semi-axes U(0.6,1.0)) on a jittered 13^3 lattice in a "
+        "40^3 box, kappa=8, m=600 n=150 k=300 p=601 per body (N=600,000), 4 plane waves; "
+        "S build of 2000 unique shapes + capped mixed solve"),
+}
+WORKLOAD = WORKLOADS[1]
+# convention: one pair = one phi plus a complex multiply-add (8 flops) into every
+# right-hand side; phi = 35 flops in 2D, 15 in 3D (FFMA = 2, special function = 1)
+FLOPS_PER_PAIR = {2: lambda nrhs: 35 + 8 * nrhs, 3: lambda nrhs: 15 + 8 * nrhs}
+FLOPS_PER_PAIR_2D = FLOPS_PER_PAIR[2]
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
 # DRAM bytes (read + write) of one launch on this workload, from one ncu capture
 # (profiles/g_umma_kernel_2d_1000bodies_8rhs.md); null for kernels not captured
@@ -50,10 +68,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mbs", choices=["mbs", "reference"])
-    ap.add_argument("--tol", type=float, default=1e-11)
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3],
+                    help="workload: 1 the 1000-body 2D headline workload (default), 2 the 10,000-body "
+                         "2D workload, 3 the 2000-ellipsoid 3D workload")
+    ap.add_argument("--capped-iters", type=int, default=20,
+                    help="configs 2/3: block-GMRES steps of the capped mixed solve in each step")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="relative residual of the solve: default 1e-11 on the 1000-body workload, "
+                         "1e-9 (the metric's accuracy) on the two large ones")
     ap.add_argument("--restart", type=int, default=200)
-    ap.add_argument("--fp64-kernel", type=int, default=0, choices=[0, 1],
-                    help="FP64-accurate G_hat: 0 on the FP64 pipe, 1 in double-float on the FP32 pipe")
+    ap.add_argument("--fp64-kernel", type=int, default=2, choices=[0, 1, 2],
+                    help="FP64-accurate G_hat: 2 automatic (default: double-float on the FP32 pipe where "
+                         "the solve's tolerance allows it), 1 double-float, 0 FP64 pipe")
     ap.add_argument("--inner-tol", type=float, default=1e-4,
                     help="relative tolerance of each FP32 inner solve of the mixed refinement "
                          "(1e-4 reaches 1e-11 in 3 sweeps with the fewest inner iterations)")
@@ -62,8 +88,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=1,
                     help="steps of the end-to-end (host buffers) measurement")
-    ap.add_argument("--fp64-iters", type=int, default=12,
-                    help="iterations of the capped FP64 solve used for its time estimate")
+    ap.add_argument("--fp64-max-iter", type=int, default=8000,
+                    help="iteration cap of the measured plain-FP64 solve (config 1)")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the served trace (0 = skip); body counts scaled to 20..300")
     ap.add_argument("--serve-tmax", type=int, default=300)
@@ -71,8 +97,10 @@ def parse():
                     help="FP32 G_hat kernel (mac_path option): 0 auto (tcgen05), 1 FP32 pipe, "
                          "2 mma.sync tensor-core multiply-add, 3 tcgen05 tensor-core multiply-add")
     ap.add_argument("--kernel", choices=["g32", "g64"], default=None,
-                    help="only apply G_hat (FP32 or FP64) to 8 random vectors, steps times "
+                    help="only apply G_hat (FP32 or FP64) to nrhs random vectors, steps times "
                          "(for profiling the dominant kernel); prints per-launch times")
+    ap.add_argument("--bodies", type=int, default=0,
+                    help="with --kernel: the first B bodies of the workload only (small profiling case)")
     return ap.parse_args()
 
 
@@ -132,9 +160,11 @@ def run_kernel_only(a):
     __graft_entry__.build()
     import paper_2603_19113_gb300 as pkg
 
-    wl = mi.config1()
+    wl = {1: mi.config1, 2: mi.config2, 3: mi.config3}[a.config]()
+    if a.bodies:
+        wl = wl.subset(range(a.bodies))
     stream = torch.cuda.current_stream()
-    ctx = pkg.Context(2, wl.kappa, stream=stream.cuda_stream, mac_path=a.mac)
+    ctx = pkg.Context(wl.dim, wl.kappa, stream=stream.cuda_stream, mac_path=a.mac, fp64_kernel=a.fp64_kernel)
     ctx.build_scattering_matrices(wl)
     q = torch.randn(wl.nrhs, ctx.N, dtype=torch.complex128, device="cuda").T
     prec = pkg.PREC_FP32 if a.kernel == "g32" else pkg.PREC_FP64
@@ -145,8 +175,12 @@ def run_kernel_only(a):
     for _ in range(a.steps):
         ctx.apply_G(q, prec)
     kt = ctx.kernel_times()
-    print(json.dumps({"kernel": a.kernel, "mac_path": a.mac, "N": ctx.N, "nrhs": wl.nrhs, **kt}),
-          flush=True)
+    _, off, _ = ctx.get_layout()
+    pairs = ctx.N * ctx.N - int(np.sum(np.diff(off).astype(np.int64) ** 2))
+    ms = kt["g32_ms"] / max(1, kt["g32_launches"]) if a.kernel == "g32" else kt["g64_ms"] / max(1, kt["g64_launches"])
+    print(json.dumps({"kernel": a.kernel, "config": a.config, "bodies": wl.T, "mac_path": a.mac,
+                      "fp64_kernel": a.fp64_kernel, "N": ctx.N, "nrhs": wl.nrhs, "pairs_per_launch": pairs,
+                      "ms_per_launch": ms, "pairs_per_s": pairs / (ms / 1e3), **kt}), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -254,20 +288,26 @@ class ClockSampler:
 # CPU oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 def _oracle_rows(args):
-    import numpy as np
     import oracle as orc
-    xyz, body, q, rows, kappa = args
+    xyz, body, q, rows, kappa, dim = args
     t0 = time.perf_counter()
-    orc.G_rows(2, kappa, xyz, body, q, rows)
+    orc.G_rows(dim, kappa, xyz, body, q, rows)
     return time.perf_counter() - t0
 
 
-def oracle_sample_setup(seed=0):
+def oracle_sample_setup(seed=0, config=1):
+    """Skeleton layout of the workload for timing the oracle's G_hat rows.  The
+    1000-body workload takes the oracle's own skeletons; for the two large ones
+    (10,000 and 2000 unique shapes) every other collocation point stands in for
+    the skeleton, which leaves the number of pairs per row unchanged."""
     import numpy as np
     import mbs_inputs as mi
     import oracle as orc
-    wl = mi.config1(seed=seed)
-    sdata = orc.build_all(wl)
+    wl = {1: mi.config1, 2: mi.config2, 3: mi.config3}[config](seed=seed)
+    if config == 1:
+        sdata = orc.build_all(wl)
+    else:
+        sdata = [{"skel": np.arange(0, 2 * sh.k, 2)} for sh in wl.shapes]
     lay = orc.layout(wl, sdata)
     rng = np.random.default_rng(1)
     N = lay["xhat"].shape[0]
@@ -283,11 +323,10 @@ def oracle_pairs_per_s(pool, nproc, wl, lay, q, rows_total, seed=2):
     rows = np.sort(np.random.default_rng(seed).choice(N, rows_total, replace=False))
     chunks = np.array_split(rows, nproc * 2)
     t0 = time.perf_counter()
-    list(pool.map(_oracle_rows, [(lay["xhat"], lay["body"], q, c, wl.kappa) for c in chunks]))
+    list(pool.map(_oracle_rows, [(lay["xhat"], lay["body"], q, c, wl.kappa, wl.dim) for c in chunks]))
     dt = time.perf_counter() - t0
-    pairs = 0
-    for r in rows:
-        pairs += N - int(np.sum(lay["body"] == lay["body"][r]))
+    counts = np.bincount(lay["body"])
+    pairs = int(np.sum(N - counts[lay["body"][rows]]))
     return pairs / dt, dt, rows_total
 
 
@@ -305,8 +344,10 @@ def run_reference(a, ws, rank):
     if rank != 0:
         return
     pool, nproc = make_pool()
-    wl, lay, q = oracle_sample_setup()
-    rows = max(64, 16 * nproc)
+    wl, lay, q = oracle_sample_setup(config=a.config)
+    N = lay["xhat"].shape[0]
+    # rows of the large workloads hold ~10x the sources: fewer rows per step
+    rows = max(64, 16 * nproc) if a.config == 1 else max(32, 2 * nproc)
     for _ in range(a.warmup):
         oracle_pairs_per_s(pool, nproc, wl, lay, q, rows, seed=10)
     t0 = time.perf_counter()
@@ -317,12 +358,12 @@ def run_reference(a, ws, rank):
     total = time.perf_counter() - t0
     pool.close()
     value = statistics.mean(rates)
-    sample = f"oracle G_hat rows: {rows} random target rows x 64,000 sources x 8 RHS per step"
+    sample = f"oracle G_hat rows: {rows} random target rows x {N:,} sources x {wl.nrhs} RHS per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "CPU oracle (numpy/scipy)"},
+        "data": "synthetic", "config": {"workload": WORKLOADS[a.config], "reference": "CPU oracle (numpy/scipy)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -348,12 +389,15 @@ def run_mbs(a, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    wl = mi.config1(seed=rank)
+    cfg = a.config
+    capped = cfg != 1
+    wl = {1: mi.config1, 2: mi.config2, 3: mi.config3}[cfg](seed=rank)
+    dim = wl.dim
     v_host = wl.boundary_data()
     tg_host = mi.far_targets(wl, a.targets, mode="ring")
     M = tg_host.shape[0]
     nrhs = wl.nrhs
-    # device-resident inputs (column-major (rows, nrhs) complex128; targets (M, 2))
+    # device-resident inputs (column-major (rows, nrhs) complex128; targets (M, dim))
     v_dev = torch.from_numpy(np.ascontiguousarray(v_host.T)).to(dev).T
     tg_dev = torch.from_numpy(np.ascontiguousarray(tg_host.T)).to(dev).T
     # pinned host inputs for the end-to-end measurement
@@ -361,14 +405,22 @@ def run_mbs(a, ws, rank, local):
     tg_pin = torch.from_numpy(np.ascontiguousarray(tg_host.T)).pin_memory().T
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=a.inner_tol, restart=a.restart, fp64_kernel=a.fp64_kernel,
-                max_iter=50000, max_sweeps=12, stream=stream.cuda_stream, mac_path=a.mac)
-    ctx = pkg.Context(2, wl.kappa, **opts)
+    opts = dict(precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=a.inner_tol, restart=a.restart,
+                fp64_kernel=a.fp64_kernel, max_iter=50000, max_sweeps=12, stream=stream.cuda_stream,
+                mac_path=a.mac)
+    if capped:
+        # a fixed amount of solve work per step: capped_iters block-GMRES steps in
+        # one refinement sweep, then its FP64 residual
+        opts.update(max_iter=a.capped_iters, max_sweeps=1, restart=max(a.capped_iters, 1))
+    ctx = pkg.Context(dim, wl.kappa, **opts)
+    build_s = []
 
     def step(v, tg):
-        ctx.build_scattering_matrices(wl)
+        t0 = time.perf_counter()
+        ctx.build_scattering_matrices(wl)  # returns after the device work
+        build_s.append(time.perf_counter() - t0)
         b = ctx.rhs(v)
-        q, info = ctx.solve(b)
+        q, info = ctx.solve(b, raise_on_noconv=not capped)
         u = ctx.evaluate_field(tg, q)
         return info, u
 
@@ -380,6 +432,7 @@ def run_mbs(a, ws, rank, local):
     for _ in range(a.warmup):
         flush.zero_()
         info, _ = step(v_dev, tg_dev)
+    build_s.clear()
 
     # ---- timed region: device-resident inputs ----
     sampler = ClockSampler(local)
@@ -394,9 +447,10 @@ def run_mbs(a, ws, rank, local):
     e0.record(stream)
     pairs = 0
     infos = []
+    u_mixed = None
     for _ in range(a.steps):
         flush.zero_()
-        info, u = step(v_dev, tg_dev)
+        info, u_mixed = step(v_dev, tg_dev)
         infos.append(info)
         pairs += (info["matvecs_fp32"] + info["matvecs_fp64"]) * pairs_mv + M * N
     e1.record(stream)
@@ -422,7 +476,7 @@ def run_mbs(a, ws, rank, local):
         flush.zero_()
         ctx.build_scattering_matrices(wl)
         b = ctx.rhs(v_pin)                 # H2D v, D2H b
-        q, info = ctx.solve(b)             # H2D b (and x0), D2H q
+        q, info = ctx.solve(b, raise_on_noconv=not capped)  # H2D b (and x0), D2H q
         u = ctx.evaluate_field(tg_pin, q)  # H2D targets and q, D2H u
         e_pairs += (info["matvecs_fp32"] + info["matvecs_fp64"]) * pairs_mv + M * N
         h2d += v_pin.numel() * 16 + 2 * b.numel() * 16 + q.numel() * 16 + tg_pin.numel() * 8
@@ -431,27 +485,32 @@ def run_mbs(a, ws, rank, local):
     e_dt = reduce_max(time.perf_counter() - t0, ws, dev)
     e_value = reduce_sum(e_pairs, ws, dev) / e_dt
 
-    # ---- FP64 path: time to the same tolerance (one solve) ----
     t2s = {"mixed_s": statistics.mean(i["seconds"] for i in infos),
            "mixed_inner_iterations": infos[-1]["inner_iterations"],
            "mixed_sweeps": infos[-1]["sweeps"], "mixed_rel_residual": infos[-1]["rel_residual"],
+           "mixed_fp64_kernel": "double-float" if infos[-1]["fp64_kernel"] else "FP64 pipe",
            "tol": a.tol}
-    if not a.no_fp64 and rank == 0:
-        # The plain FP64 path on this workload needs thousands of FP64 operator
-        # applications (~0.83 s each on GB300); time a capped FP64 solve and
-        # scale its per-iteration time by the mixed solve's inner iteration count.
-        ctx64 = pkg.Context(2, wl.kappa, precision=pkg.PREC_FP64, tol=a.tol, restart=a.restart, fp64_kernel=a.fp64_kernel,
-                            max_iter=a.fp64_iters, stream=stream.cuda_stream)
+    if capped:
+        t2s = {"capped_solve_s": t2s["mixed_s"], "block_gmres_steps": infos[-1]["inner_iterations"],
+               "rel_residual_after_cap": infos[-1]["rel_residual"],
+               "fp64_kernel": t2s["mixed_fp64_kernel"],
+               "note": "time to solution not measured on this workload: thousands of iterations"}
+    if cfg == 1 and not a.no_fp64 and rank == 0:
+        # ---- the plain FP64 path to the same tolerance, measured (one solve) ----
+        ctx64 = pkg.Context(2, wl.kappa, precision=pkg.PREC_FP64, tol=a.tol, restart=a.restart,
+                            fp64_kernel=a.fp64_kernel, max_iter=a.fp64_max_iter, stream=stream.cuda_stream)
         ctx64.build_scattering_matrices(wl)
         b64 = ctx64.rhs(v_dev)
         q64, i64 = ctx64.solve(b64, raise_on_noconv=False)
-        per_it = i64["seconds"] / max(1, i64["inner_iterations"])
-        t2s.update({"fp64_s_estimated": per_it * infos[-1]["inner_iterations"],
-                    "fp64_estimate_method": f"{i64['inner_iterations']}-iteration FP64 solve: "
-                    f"{per_it:.3f} s/iteration x mixed inner iterations",
-                    "fp64_s_per_iteration": per_it})
+        u64 = ctx64.evaluate_field(tg_dev, q64)
         ctx64.close()
-        # both paths to convergence on the 10-body workload (small enough for FP64)
+        t2s.update({"fp64_s": i64["seconds"], "fp64_iterations": i64["inner_iterations"],
+                    "fp64_rel_residual": i64["rel_residual"], "fp64_converged": bool(i64["converged"]),
+                    "fp64_kernel": "double-float" if i64["fp64_kernel"] else "FP64 pipe",
+                    "fp64_over_mixed": i64["seconds"] / t2s["mixed_s"],
+                    "field_rel_err_vs_fp64": float((u_mixed - u64).abs().max() / u64.abs().max()),
+                    "field_targets": M})
+        # both paths to convergence on the 10-body workload as well
         wl0 = mi.config0()
         v0 = torch.from_numpy(np.ascontiguousarray(wl0.boundary_data().T)).to(dev).T
         tg0 = torch.from_numpy(np.ascontiguousarray(mi.far_targets(wl0, 256).T)).to(dev).T
@@ -471,49 +530,60 @@ def run_mbs(a, ws, rank, local):
                               float((u64 - umx).abs().max() / u64.abs().max())}
 
     # ---- roofline of the dominant kernel (FP32 G_hat) ----
-    flops_launch = pairs_mv * FLOPS_PER_PAIR_2D(nrhs)
+    flops_launch = pairs_mv * FLOPS_PER_PAIR[dim](nrhs)
     avg_ms = kt["g32_ms"] / max(1, kt["g32_launches"])
     achieved = flops_launch / (avg_ms / 1e3) / 1e12
-    kname = {1: "g_f32_kernel<2,8,2>", 2: "g_tc_kernel<2,1>", 3: "g_umma_kernel<2,8>"}.get(
-        kt["g32_path"], "unknown")
+    nr = 16 if nrhs >= 16 else 8
+    kname = {1: f"g_f32_kernel<{dim},{min(nrhs, 8)},2>", 2: f"g_tc_kernel<{dim},1>",
+             3: f"g_umma_kernel<{dim},{nr}>"}.get(kt["g32_path"], "unknown")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": TRAFFIC_BYTES.get(kname), "avg_launch_ms": avg_ms,
                 "launches": kt["g32_launches"], "nsplit": kt["g32_nsplit"],
                 "flops_per_launch": flops_launch,
+                "pairs_per_s": pairs_mv / (avg_ms / 1e3),
                 "peak_note": "FP32 SIMT peak from unit counts: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     share = kt["g32_ms"] / ms if ms > 0 else None
+    g64_share = kt["g64_ms"] / ms if ms > 0 else None
 
     served = None
-    if rank == 0 and a.serve_requests > 0:
+    if rank == 0 and a.serve_requests > 0 and cfg == 1:
         served = run_serving(a, pkg, mi)
 
     cpu = None
     if pool is not None:
         import oracle  # noqa: F401  (test infrastructure: CPU baseline leg only)
-        wlo, lay, qo = oracle_sample_setup()
-        rows = max(64, 32 * nproc)
+        wlo, lay, qo = oracle_sample_setup(config=cfg)
+        rows = max(64, 32 * nproc) if cfg == 1 else max(32, 4 * nproc)
+        # one untimed pass first: the spawned workers import numpy, scipy and the oracle
+        oracle_pairs_per_s(pool, nproc, wlo, lay, qo, 2 * nproc, seed=3)
         rate, dt, _ = oracle_pairs_per_s(pool, nproc, wlo, lay, qo, rows)
         pool.close()
         cpu = {"value": rate, "unit": UNIT, "cores": nproc, "kind": "oracle",
-               "sample": f"oracle G_hat rows: {rows} random target rows x 64,000 sources x 8 RHS "
+               "sample": f"oracle G_hat rows: {rows} random target rows x {N:,} sources x {nrhs} RHS "
                          f"({dt:.1f} s wall on {nproc} processes)"}
 
     if rank == 0:
+        config = {"workload": WORKLOADS[cfg], "N": N, "pairs_per_matvec": pairs_mv, "nrhs": nrhs,
+                  "field_targets": M, "restart": opts["restart"], "inner_tol": a.inner_tol,
+                  "fp64_kernel": {0: "FP64 pipe", 1: "double-float on the FP32 pipe",
+                                  2: "automatic (double-float where the tolerance allows)"}[a.fp64_kernel],
+                  "l2": "256 MiB buffer written before every step",
+                  "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+        if capped:
+            config["capped_solve"] = f"{a.capped_iters} block-GMRES steps + 1 FP64 residual per step"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "pairs_per_matvec": pairs_mv, "nrhs": nrhs,
-                       "field_targets": M, "restart": a.restart, "inner_tol": a.inner_tol,
-                       "fp64_kernel": "double-float on the FP32 pipe" if a.fp64_kernel else "FP64 pipe",
-                       "l2": "256 MiB buffer written before every step",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "config": config,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(1, e_steps),
                     "d2h_bytes_per_step": d2h // max(1, e_steps), "steps": e_steps},
             "roofline": roofline,
             "g32_time_share": share,
+            "g64_time_share": g64_share,
+            "s_build_s": statistics.mean(build_s) if build_s else None,
             "time_to_solution": t2s,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -526,6 +596,8 @@ def run_mbs(a, ws, rank, local):
 
 def main():
     a = parse()
+    if a.tol is None:
+        a.tol = 1e-11 if a.config == 1 else 1e-9
     ws, rank, local = dist_setup()
     if a.kernel:
         run_kernel_only(a)
