@@ -14,6 +14,8 @@
 #include "bessel_coeffs.h"
 #include "common.cuh"
 
+__device__ __constant__ float c_f32_64F[MBS_F32_X64_DEG + 1] = MBS_F32_X64_F;
+__device__ __constant__ float c_f32_64G[MBS_F32_X64_DEG + 1] = MBS_F32_X64_G;
 __device__ __constant__ float c_f32_8F[MBS_F32_X8_DEG + 1] = MBS_F32_X8_F;
 __device__ __constant__ float c_f32_8G[MBS_F32_X8_DEG + 1] = MBS_F32_X8_G;
 __device__ __constant__ float c_f32_F[MBS_F32_X3_DEG + 1] = MBS_F32_X3_F;

@@ -20,6 +20,7 @@ mp.mp.dps = 40
 
 # (name, xa, degree, precision)
 FITS = [
+    ("F32_X64", 64.0, 2, "float"),
     ("F32_X8", 8.0, 4, "float"),
     ("F32_X3", 3.0, 6, "float"),
     ("F64_X4", 4.0, 20, "double"),

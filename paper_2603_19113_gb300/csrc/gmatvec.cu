@@ -43,8 +43,13 @@ __global__ void pair_table_kernel(int dim, int T, const double* __restrict__ c,
     const double dz = dim == 3 ? c[3 * a + 2] - c[3 * b + 2] : 0.0;
     const double R = sqrt(dx * dx + dy * dy + dz * dz);
     if (dim == 2) {
-        const double ph = fmod(kappa * R + 0.25 * MBS_PI, MBS_TWO_PI);
-        const bool near = kappa * (R - brad[a] - brad[b]) < 8.0 * (1.0 + 1e-6);
+        // phase in [0, 2 pi); body pairs whose points are all at kappa r >= 64
+        // store the same phase minus 2 pi (negative): the FP32 kernels may then
+        // use the shorter x >= 64 fit of H0
+        double ph = fmod(kappa * R + 0.25 * MBS_PI, MBS_TWO_PI);
+        const double gap = kappa * (R - brad[a] - brad[b]);
+        const bool near = gap < 8.0 * (1.0 + 1e-6);
+        if (gap >= 64.0 * (1.0 + 1e-6)) ph -= MBS_TWO_PI;
         pair[idx] = make_float4((float)dx, (float)dy, near ? -(float)R : (float)R, (float)ph);
     } else {
         pair[idx] = make_float4((float)dx, (float)dy, (float)dz, (float)R);

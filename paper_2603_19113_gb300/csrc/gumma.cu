@@ -211,26 +211,32 @@ __global__ void __launch_bounds__(128) g_umma_pack_kernel(const GLayout L, const
 
 // phi of the point pair (target i, staged source sj) for a far body pair,
 // with the per-(target, body) constants of the expanded form (see above).
-template <int DIM>
+// 2D: VF selects the x >= 64 fit of H0 (degree 2) for body pairs whose points
+// are all that far apart, else the x >= 8 fit (degree 4) (modulus fits with
+// the amplitude constant folded in, in K); glast is the last phase
+// coefficient plus the body-pair phase.
+template <int DIM, bool VF>
 __device__ __forceinline__ float2 far_pair(const float4 sj, const float A0, const float Bx,
                                            const float By, const float Bz, const float R,
                                            const float R2, const float glast, const float phi0,
-                                           const float (&fcoef)[MBS_F32_X8_DEG + 1],
                                            const F32Const& K) {
     if (DIM == 2) {
+        constexpr int DEG = VF ? MBS_F32_X64_DEG : MBS_F32_X8_DEG;
+        const float* gc = VF ? c_f32_64G : c_f32_8G;
+        const float* fcoef = VF ? K.f64a : K.f8a;
         const float s = fmaf(Bx, sj.x, fmaf(By, sj.y, A0 + sj.w));
         const float r2 = R2 + s;
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
         const float dr = __fdividef(s, r + R);
-        const float u = fmaf(K.c8, rinv, -1.f);
-        float f = fcoef[0], gp = c_f32_8G[0];
+        const float u = fmaf(VF ? K.c64 : K.c8, rinv, -1.f);
+        float f = fcoef[0], gp = gc[0];
 #pragma unroll
-        for (int k = 1; k < MBS_F32_X8_DEG; ++k) {
+        for (int k = 1; k < DEG; ++k) {
             f = fmaf(f, u, fcoef[k]);
-            gp = fmaf(gp, u, c_f32_8G[k]);
+            gp = fmaf(gp, u, gc[k]);
         }
-        f = fmaf(f, u, fcoef[MBS_F32_X8_DEG]);
+        f = fmaf(f, u, fcoef[DEG]);
         gp = fmaf(gp, u, glast);
         const float2 e = expi_f32(fmaf(K.kappa, dr, gp));
         const float amp = f * rsqrtf(r);
@@ -394,9 +400,6 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
         const float q2i = fmaf(di[0], di[0], fmaf(di[1], di[1], di[2] * di[2]));
         const uint32_t a_lane = tmem + ((uint32_t)(warp * 32) << 16);
 
-        float fcoef[MBS_F32_X8_DEG + 1];  // modulus fit with the amplitude constant folded in
-#pragma unroll
-        for (int k = 0; k <= MBS_F32_X8_DEG; ++k) fcoef[k] = c_f32_8F[k] * K.ampc;
 
         float accr[NR], acci[NR];
 #pragma unroll
@@ -452,12 +455,14 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                 phi0 = f0_cur;
             }
             const bool wfast = __all_sync(0xffffffffu, act && !near);  // warp-uniform fast path
+            // 2D: every pair of the body pair at kappa r >= 64 (phase stored minus 2 pi)
+            const bool wvfar = DIM == 2 && __all_sync(0xffffffffu, act && !near && P.w < 0.f);
             const float R = DIM == 2 ? P.z : P.w;
             const float R2 = R * R;
             const float Dz = DIM == 3 ? P.z : 0.f;
             const float Bx = -2.f * (P.x + di[0]), By = -2.f * (P.y + di[1]), Bz = -2.f * (Dz + di[2]);
             const float A0 = fmaf(2.f * P.x, di[0], fmaf(2.f * P.y, di[1], fmaf(2.f * Dz, di[2], q2i)));
-            const float glast = c_f32_8G[MBS_F32_X8_DEG] + phi0;  // phase fit with the body-pair phase
+            const float glast = (wvfar ? c_f32_64G[MBS_F32_X64_DEG] : c_f32_8G[MBS_F32_X8_DEG]) + phi0;
 
             for (int c = cb; c < ce; ++c, ++g) {
                 if (!mbar_wait(smem_u32(&bar_full[stage]), fphase)) s_abort = 1;
@@ -469,11 +474,19 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                     // A columns of sources 8 half .. 8 half + 7:
                     // [hi re/im of 4 sources | their lo | hi of the next 4 | lo]
                     uint32_t av[32];
-                    if (full_fast) {
+                    if (full_fast && wvfar) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const float2 p = far_pair<DIM>(src[8 * half + j], A0, Bx, By, Bz, R, R2, glast,
-                                                           phi0, fcoef, K);
+                            const float2 p = far_pair<DIM, true>(src[8 * half + j], A0, Bx, By, Bz, R, R2,
+                                                                 glast, phi0, K);
+                            const int o = (j >> 2) * 16 + (j & 3) * 2;
+                            split_tf32(p, av[o], av[o + 1], av[o + 8], av[o + 9]);
+                        }
+                    } else if (full_fast) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 p = far_pair<DIM, false>(src[8 * half + j], A0, Bx, By, Bz, R, R2,
+                                                                  glast, phi0, K);
                             const int o = (j >> 2) * 16 + (j & 3) * 2;
                             split_tf32(p, av[o], av[o + 1], av[o + 8], av[o + 9]);
                         }
@@ -486,7 +499,8 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                             if (js >= cnt) {
                                 // padding of a ragged last chunk: q = 0 there
                             } else if (act && !near) {
-                                p = far_pair<DIM>(sj, A0, Bx, By, Bz, R, R2, glast, phi0, fcoef, K);
+                                p = wvfar ? far_pair<DIM, true>(sj, A0, Bx, By, Bz, R, R2, glast, phi0, K)
+                                          : far_pair<DIM, false>(sj, A0, Bx, By, Bz, R, R2, glast, phi0, K);
                             } else if (act) {
                                 const float dj[3] = {sj.x, sj.y, sj.z};
                                 p = pair_phi_f32<DIM, false>(di, dj, P, R2, phi0, K);

@@ -18,6 +18,12 @@ struct F32Const {
     float ampc;   // (1/4) sqrt(2 / (pi kappa))
     float c8;     // 2 * 8 / kappa  (u = c8 / r - 1 for the x >= 8 fit)
     float c3;     // 2 * 3 / kappa
+    float c64;    // 2 * 64 / kappa (the x >= 64 fit)
+    // modulus fits with the amplitude constant ampc folded in; a kernel takes
+    // F32Const by value, so these sit in its parameter space (constant bank)
+    // and multiply-adds read them without registers
+    float f8a[MBS_F32_X8_DEG + 1];
+    float f64a[MBS_F32_X64_DEG + 1];
 };
 
 inline F32Const make_f32const(double kappa) {
@@ -26,17 +32,22 @@ inline F32Const make_f32const(double kappa) {
     K.ampc = (float)(0.25 * sqrt(2.0 / (MBS_PI * kappa)));
     K.c8 = (float)(2.0 * MBS_F32_X8_XA / kappa);
     K.c3 = (float)(2.0 * MBS_F32_X3_XA / kappa);
+    K.c64 = (float)(2.0 * MBS_F32_X64_XA / kappa);
+    const float f8[] = MBS_F32_X8_F, f64[] = MBS_F32_X64_F;
+    for (int k = 0; k <= MBS_F32_X8_DEG; ++k) K.f8a[k] = f8[k] * K.ampc;
+    for (int k = 0; k <= MBS_F32_X64_DEG; ++k) K.f64a[k] = f64[k] * K.ampc;
     return K;
 }
 
-// exp(i ph) reduced to [-pi, pi] by a two-constant Cody-Waite step (6.28125 is
-// exact in 8 bits, so n * 6.28125 is exact for the |n| < 2^16 that occur).
+// exp(i ph) reduced to [-pi, pi] by one Cody-Waite step with the FP32 value
+// of 2 pi.  The constant's error, 1.7e-7, times n = ph / 2 pi adds at most
+// 2.8e-8 |ph| to the reduced phase: below the FP32 rounding of ph itself
+// (up to 6e-8 |ph|), so a second, exact-split constant buys no accuracy.
 __device__ __forceinline__ float2 expi_f32(float ph) {
     // n = nearest integer to ph / (2 pi), by adding and removing 1.5 * 2^23
     // (exact for |ph / 2 pi| < 2^22; keeps the rounding off the XU pipe)
     const float n = fmaf(ph, 0.159154943091895336f, 12582912.f) - 12582912.f;
-    ph = fmaf(-n, 6.28125f, ph);
-    ph = fmaf(-n, 1.93530717958647692e-3f, ph);
+    ph = fmaf(-n, 6.28318530717958648f, ph);
     float sn, cs;
     __sincosf(ph, &sn, &cs);
     return make_float2(cs, sn);

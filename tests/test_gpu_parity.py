@@ -106,15 +106,23 @@ def test_G_2d_fp64_and_fp32(pkg, nrhs, fp64_kernel):
 
 
 @pytest.mark.parametrize("mac_path", [1, 2, 3])
-@pytest.mark.parametrize("dim,nrhs", [(2, 8), (2, 5), (2, 16), (2, 1), (3, 8), (3, 11), (3, 2)])
-def test_G_fp32_multiply_add_paths(pkg, mac_path, dim, nrhs):
+@pytest.mark.parametrize("dim,nrhs,kappa", [(2, 8, 6.0), (2, 5, 6.0), (2, 16, 6.0), (2, 1, 6.0), (2, 8, 30.0),
+                                            (2, 16, 30.0), (3, 8, 3.0), (3, 11, 3.0), (3, 2, 3.0)])
+def test_G_fp32_multiply_add_paths(pkg, mac_path, dim, nrhs, kappa):
     """Every FP32 G_hat kernel (FP32 pipe; mma.sync and tcgen05 tensor-core
     multiply-add with the 3xTF32 split) against the oracle, with right-hand-side
     counts that fill, pad and span two blocks of right-hand sides (fewer than 4
-    right-hand sides take the FP32 pipe on every path)."""
-    wl = (mi.tiny_2d(seed=4, T=9, kappa=6.0, ks=(24, 37, 50)) if dim == 2
-          else mi.tiny_3d(seed=1, T=5, kappa=3.0, nth=10, nph=14, p=141, k=70))
+    right-hand sides take the FP32 pipe on every path).  At kappa = 30 the
+    nearest body pairs come to kappa r ~ 30 (the x >= 8 fit of H0) and the
+    others stay beyond kappa r = 64 (the x >= 64 fit)."""
+    wl = (mi.tiny_2d(seed=4, T=9, kappa=kappa, ks=(24, 37, 50)) if dim == 2
+          else mi.tiny_3d(seed=1, T=5, kappa=kappa, nth=10, nph=14, p=141, k=70))
     ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, mac_path=mac_path)
+    if kappa == 30.0:  # both fits occur
+        cen, rho = wl.centres[:, :2], np.array([wl.shapes[s].bound_radius for s in wl.body_shape])
+        gap = kappa * (np.linalg.norm(cen[:, None] - cen[None], axis=2) - rho[:, None] - rho[None])
+        off = ~np.eye(wl.T, dtype=bool)
+        assert gap[off].min() < 64.0 < gap[off].max()
     q = _rand((ctx.N, nrhs), 13)
     G = orc.G_dense(dim, wl.kappa, lay["xhat"], lay["body"])
     ref = G @ q
