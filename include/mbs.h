@@ -89,6 +89,9 @@ typedef struct mbs_options {
                             double-float when 1e-14 ||S||_F (the FP64 residual floor it leaves, with the
                             root mean square of ||S_tau||_F over the bodies) is at most tol / 10, else
                             the FP64 pipe; apply calls use the FP64 pipe */
+    int sbuild_threads;  /* threads per CTA of the S build (128, 256 or 512); 0 (default): 256 (the build
+                            is FP64-pipe-bound: the three sizes measured within 2 % on GB300); -1: tuned on the
+                            first build of a size class (when autotune is on), at the cost of ~half a build */
 } mbs_options;
 
 typedef struct mbs_shape {
@@ -305,7 +308,8 @@ mbs_status mbs_profile(mbs_ctx* ctx, int enable);
  * out[0] = total ms of FP32 G_hat launches, out[1] = their count,
  * out[2] = total ms of FP64 G_hat launches, out[3] = their count,
  * out[4] = kernel path of the latest FP32 G_hat (mac_path numbering; 0 if
- * none), out[5] = its source-split count.  out must hold 6 doubles.
+ * none), out[5] = its source-split count, out[6] = threads per CTA of the
+ * latest S build (0 if none).  out must hold 7 doubles.
  * Synchronises the context's stream. */
 mbs_status mbs_kernel_times(mbs_ctx* ctx, double* out);
 
@@ -321,7 +325,11 @@ typedef struct mbs_request {
     const mbs_body* bodies;
     int nrhs;
     const double* v;      /* (sum m) x nrhs boundary data, host memory, copied at submit */
-    double tol;           /* relative residual target (mixed precision solve) */
+    double tol;           /* relative residual target */
+    int fp64;             /* 1: the plain FP64 path; 0: mixed precision (FP32 GMRES inside FP64
+                             refinement) */
+    int max_iter;         /* inner iteration cap of the solve (0: the library default); a request
+                             that reaches it finishes with done = 1 and converged = 0 */
 } mbs_request;
 
 typedef struct mbs_request_result {
@@ -331,6 +339,11 @@ typedef struct mbs_request_result {
     double rel_residual;
     int inner_iterations;
     double t_submit, t_start, t_end;   /* seconds on the server's clock */
+    int converged;        /* 1 if the solve reached tol */
+    double dev_start, dev_end;  /* the request's device work: CUDA events recorded on its stream
+                                   before its first and after its last kernel, seconds after the
+                                   server's creation (device clock) */
+    double g_busy_ms;     /* its G_hat kernel time (events around every G_hat launch) */
 } mbs_request_result;
 
 /* Create a server with max_active concurrent solves and an HBM budget in
@@ -343,6 +356,10 @@ mbs_status mbs_serve_submit(mbs_server* srv, const mbs_request* req, int64_t* id
 /* Poll (non-blocking) the state of a request; if it is done and qhat is not
  * NULL, copy its solution (N x nrhs complex, host memory) there. */
 mbs_status mbs_serve_poll(mbs_server* srv, int64_t id, mbs_request_result* res, double* qhat);
+/* Admission order: 0 (default) arrival order; 1 shortest estimated work first
+ * (pairs x iteration-independent cost of the S build and the operator), which
+ * lets small requests pass large ones that are still queued. */
+mbs_status mbs_serve_set_policy(mbs_server* srv, int policy);
 /* Block until every submitted request has finished. */
 mbs_status mbs_serve_drain(mbs_server* srv);
 /* Stop the worker thread and free everything. */

@@ -23,6 +23,7 @@ class mbs_options(C.Structure):
         ("ls_rcond", C.c_double), ("stream", C.c_void_p), ("hbm_budget", C.c_size_t),
         ("tile_override", C.c_int), ("block_krylov", C.c_int), ("mac_path", C.c_int),
         ("autotune", C.c_int), ("cuda_graphs", C.c_int), ("fp64_kernel", C.c_int),
+        ("sbuild_threads", C.c_int),
     ]
 
 
@@ -53,6 +54,7 @@ class mbs_request(C.Structure):
         ("dim", C.c_int), ("kappa", C.c_double), ("nshapes", C.c_int),
         ("shapes", C.POINTER(mbs_shape)), ("nbodies", C.c_int), ("bodies", C.POINTER(mbs_body)),
         ("nrhs", C.c_int), ("v", C.POINTER(C.c_double)), ("tol", C.c_double),
+        ("fp64", C.c_int), ("max_iter", C.c_int),
     ]
 
 
@@ -60,7 +62,8 @@ class mbs_request_result(C.Structure):
     _fields_ = [
         ("done", C.c_int), ("status", C.c_int), ("N", C.c_int64), ("rel_residual", C.c_double),
         ("inner_iterations", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double),
-        ("t_end", C.c_double),
+        ("t_end", C.c_double), ("converged", C.c_int), ("dev_start", C.c_double),
+        ("dev_end", C.c_double), ("g_busy_ms", C.c_double),
     ]
 
 
@@ -95,6 +98,7 @@ SIGNATURES = {
     "mbs_serve_submit": (C.c_int, [_P, C.POINTER(mbs_request), C.POINTER(C.c_int64)]),
     "mbs_serve_poll": (C.c_int, [_P, C.c_int64, C.POINTER(mbs_request_result), _P]),
     "mbs_serve_drain": (C.c_int, [_P]),
+    "mbs_serve_set_policy": (C.c_int, [_P, C.c_int]),
     "mbs_serve_destroy": (None, [_P]),
 }
 

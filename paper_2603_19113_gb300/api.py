@@ -348,10 +348,11 @@ def _ctx_profile(self, enable: bool = True):
 
 
 def _ctx_kernel_times(self) -> dict:
-    out = (C.c_double * 6)()
+    out = (C.c_double * 7)()
     self._check(_lib().mbs_kernel_times(self._h, out))
     return {"g32_ms": out[0], "g32_launches": int(out[1]), "g64_ms": out[2],
-            "g64_launches": int(out[3]), "g32_path": int(out[4]), "g32_nsplit": int(out[5])}
+            "g64_launches": int(out[3]), "g32_path": int(out[4]), "g32_nsplit": int(out[5]),
+            "sbuild_threads": int(out[6])}
 
 
 Context.profile = _ctx_profile
@@ -377,7 +378,13 @@ class Server:
             raise MbsError(st, "mbs_serve_create")
         self._keep = {}
 
-    def submit(self, wl, v, tol: float = 1e-10) -> int:
+    def set_policy(self, policy: int):
+        """0: admit in arrival order; 1: shortest estimated work first."""
+        st = _lib().mbs_serve_set_policy(self._h, policy)
+        if st != L.MBS_OK:
+            raise MbsError(st, "mbs_serve_set_policy")
+
+    def submit(self, wl, v, tol: float = 1e-10, fp64: bool = False, max_iter: int = 0) -> int:
         shapes, bodies, keep = shapes_bodies_from_workload(wl)
         vb = np.ascontiguousarray(np.asarray(v, dtype=np.complex128).T)
         req = L.mbs_request()
@@ -387,6 +394,8 @@ class Server:
         req.nrhs = vb.shape[0]
         req.v = vb.ctypes.data_as(C.POINTER(C.c_double))
         req.tol = tol
+        req.fp64 = 1 if fp64 else 0
+        req.max_iter = max_iter
         rid = C.c_int64()
         st = _lib().mbs_serve_submit(self._h, C.byref(req), C.byref(rid))
         if st != L.MBS_OK:

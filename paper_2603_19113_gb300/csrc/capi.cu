@@ -120,6 +120,7 @@ struct mbs_ctx {
     cudaEvent_t cap_e0 = nullptr, cap_e1 = nullptr;
     double graph_ms[2] = {0.0, 0.0};  // profiled G_hat time of replayed steps (FP32, FP64)
     int last_path = 0, last_nsplit = 0;  // launch shape of the latest FP32 G_hat
+    int last_sbuild_threads = 0;         // CTA size of the last S build
     long long graph_n[2] = {0, 0};
 
     // allocations
@@ -385,6 +386,55 @@ struct Shape32 {
     int path;
     int nsplit;
 };
+
+// Threads per CTA of the persistent S build (128, 256 or 512).  The build is
+// bound by GB300's FP64 pipe: on the 2000-ellipsoid and 10,000-body workloads
+// the three sizes measured within 2 % of each other (22.0-22.5 s and
+// 9.6-9.8 s), so the default is a fixed 256 and the probe below, which costs
+// about half a build per new size class, runs only with sbuild_threads = -1.
+// The probe times each candidate on a prefix of the jobs large enough to fill
+// the GPU with the smallest CTAs and keeps the fastest in a process-wide table
+// keyed by device, dimension and the power-of-two buckets of the largest
+// matrix dimension and of the shape count (the probe's outputs are
+// overwritten by the full build).  Different CTA sizes sum in different
+// orders; the table keeps every later build of a class reproducible.
+std::mutex g_sb_tune_mu;
+std::map<std::array<int, 4>, int> g_sb_tune;
+
+int log2_bucket(int64_t v);
+
+int sbuild_threads(mbs_ctx* c, SBuildJob* d_jobs, int nj, int* d_counter, int rows_max) {
+    if (c->opt.sbuild_threads > 0) return c->opt.sbuild_threads;
+    if (c->opt.sbuild_threads == 0 || !c->opt.autotune) return 256;
+    int dev = 0;
+    MBS_CUDA_TRY(cudaGetDevice(&dev));
+    const std::array<int, 4> key{dev, c->dim, log2_bucket(rows_max), log2_bucket(nj)};
+    std::lock_guard<std::mutex> lk(g_sb_tune_mu);
+    auto it = g_sb_tune.find(key);
+    if (it != g_sb_tune.end()) return it->second;
+    const int nprobe = std::min(nj, 4 * mbs_num_sms());
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    int best = 512;
+    float best_ms = 0.f;
+    bool first = true;
+    for (int th : {512, 256, 128}) {
+        MBS_CUDA_TRY(cudaEventRecord(a, c->st));
+        launch_sbuild(c->dim, d_jobs, nprobe, d_counter, rows_max, th, c->kappa, c->opt.ls_rcond, c->st);
+        MBS_CUDA_TRY(cudaEventRecord(b, c->st));
+        MBS_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        MBS_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (first || ms < best_ms) {
+            best_ms = ms;
+            best = th;
+            first = false;
+        }
+    }
+    c->ev_pool.push_back(a);
+    c->ev_pool.push_back(b);
+    g_sb_tune[key] = best;
+    return best;
+}
 
 std::mutex g_tune_mu;
 std::map<std::array<int, 6>, Shape32> g_tune;
@@ -1100,6 +1150,9 @@ void validate_options(const mbs_options& o) {
         throw MbsError{MBS_ERR_ARG, "mac_path must be 0, 1, 2 or 3"};
     if (o.fp64_kernel < 0 || o.fp64_kernel > 2)
         throw MbsError{MBS_ERR_ARG, "fp64_kernel must be 0, 1 or 2"};
+    if (o.sbuild_threads != 0 && o.sbuild_threads != -1 && o.sbuild_threads != 128 && o.sbuild_threads != 256 &&
+        o.sbuild_threads != 512)
+        throw MbsError{MBS_ERR_ARG, "sbuild_threads must be 0, -1, 128, 256 or 512"};
 }
 
 template <typename F>
@@ -1445,9 +1498,14 @@ void build(mbs_ctx* c, int nshapes, const mbs_shape* shapes, int nbodies, const 
     std::vector<int> used;
     for (int s = 0; s < nshapes; ++s)
         if (c->shapes[s].used) used.push_back(s);
-    std::sort(used.begin(), used.end(), [&](int a, int b2) {
-        return (int64_t)c->shapes[a].m * c->shapes[a].p > (int64_t)c->shapes[b2].m * c->shapes[b2].p;
-    });
+    // longest processing time first: the persistent build kernel takes the jobs
+    // in this order, so the big ones start first and the small ones fill the tail
+    auto work = [&](int i) {
+        const ShapeHost& h = c->shapes[i];
+        const double p = h.p, m = h.m, n = h.n, r = std::min(h.p, h.m);
+        return p * (m + n) * r + m * r * r + 10.0 * n * n * n;  // QR of B | D, of R_B^H, Jacobi
+    };
+    std::stable_sort(used.begin(), used.end(), [&](int a, int b2) { return work(a) > work(b2); });
     const size_t ws_budget = (size_t)8 << 30;
     size_t pos = 0;
     while (pos < used.size()) {
@@ -1522,9 +1580,12 @@ void build(mbs_ctx* c, int nshapes, const mbs_shape* shapes, int nbodies, const 
             mmax = std::max(mmax, s.m);
         }
         SBuildJob* d_jobs = (SBuildJob*)talloc(sizeof(SBuildJob) * nj);
+        int* d_counter = (int*)talloc(3 * sizeof(int));
         MBS_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(SBuildJob) * nj, cudaMemcpyHostToDevice, c->st));
-        launch_sbuild_phase1(d, d_jobs, nj, pmax, c->kappa, c->opt.ls_rcond, c->st);
-        launch_sbuild_phase2(d_jobs, nj, mmax, c->opt.ls_rcond, c->st);
+        const int rows_max = std::max(pmax, mmax);
+        const int threads = sbuild_threads(c, d_jobs, nj, d_counter, rows_max);
+        launch_sbuild(d, d_jobs, nj, d_counter, rows_max, threads, c->kappa, c->opt.ls_rcond, c->st);
+        c->last_sbuild_threads = threads;
         MBS_CUDA_TRY(cudaMemcpyAsync(jobs.data(), d_jobs, sizeof(SBuildJob) * nj, cudaMemcpyDeviceToHost, c->st));
         MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
         for (int j = 0; j < nj; ++j) {
@@ -1576,6 +1637,7 @@ void mbs_default_options(mbs_options* o) {
     o->autotune = 1;
     o->cuda_graphs = 1;
     o->fp64_kernel = 2;
+    o->sbuild_threads = 0;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {
@@ -1643,6 +1705,7 @@ mbs_status mbs_kernel_times(mbs_ctx* c, double* out) {
         out[3] = (double)n[1] + (double)c->graph_n[1];
         out[4] = c->last_path;
         out[5] = c->last_nsplit;
+        out[6] = c->last_sbuild_threads;
         c->graph_ms[0] = c->graph_ms[1] = 0.0;
         c->graph_n[0] = c->graph_n[1] = 0;
         return MBS_OK;

@@ -45,9 +45,12 @@
 
 namespace {
 
-constexpr int SBT = 512;  // threads per shape CTA
-constexpr int NW = SBT / 32;
+constexpr int SBT_MAX = 512;      // largest CTA size (threads per shape CTA: 128, 256 or 512)
+constexpr int NW_MAX = SBT_MAX / 32;
 constexpr double TIE = 1e-10;
+
+// warps of the CTA (the block size is chosen at launch)
+__device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -59,10 +62,10 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 }
 
 struct Red {
-    double d[NW];
-    double d2[NW];
-    int i[NW];
-    int j[NW];
+    double d[NW_MAX];
+    double d2[NW_MAX];
+    int i[NW_MAX];
+    int j[NW_MAX];
 };
 
 // Block-wide sum of a double (every thread gets the result).
@@ -73,8 +76,8 @@ __device__ double block_sum(double v, Red& r) {
     if (lane == 0) r.d[w] = v;
     __syncthreads();
     double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) t += r.d[k];
+    const int nw = nwarps();
+    for (int k = 0; k < nw; ++k) t += r.d[k];
     return t;
 }
 
@@ -86,8 +89,8 @@ __device__ double block_max(double v, Red& r) {
     if (lane == 0) r.d[w] = v;
     __syncthreads();
     double t = r.d[0];
-#pragma unroll
-    for (int k = 1; k < NW; ++k) t = fmax(t, r.d[k]);
+    const int nw = nwarps();
+    for (int k = 1; k < nw; ++k) t = fmax(t, r.d[k]);
     return t;
 }
 
@@ -110,8 +113,8 @@ __device__ int block_argmin(int key, int idx, Red& r) {
     }
     __syncthreads();
     int bk = r.i[0], bi = r.j[0];
-#pragma unroll
-    for (int k = 1; k < NW; ++k)
+    const int nw = nwarps();
+    for (int k = 1; k < nw; ++k)
         if (r.i[k] < bk || (r.i[k] == bk && r.j[k] < bi)) {
             bk = r.i[k];
             bi = r.j[k];
@@ -162,7 +165,7 @@ __device__ void householder_step(double2* A, int ld, int rows, int j, int ncols,
     }
     if (threadIdx.x == 0) diag[j] = alpha;
     __syncthreads();
-    for (int c = j + 1 + w; c < ntot; c += NW) {
+    for (int c = j + 1 + w; c < ntot; c += nwarps()) {
         double2* cc = A + (int64_t)c * ld;
         double2 d = make_double2(0.0, 0.0);
         for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(s_v[i - j], cc[i]));
@@ -199,7 +202,7 @@ __device__ void cta_apply_q(const double2* V, int ldv, int rows, int nref, doubl
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int j = nref - 1; j >= 0; --j) {
         const double2* vj = V + (int64_t)j * ldv;
-        for (int c = w; c < ncols; c += NW) {
+        for (int c = w; c < ncols; c += nwarps()) {
             double2* xc = X + (int64_t)c * ldx;
             double2 d = make_double2(0.0, 0.0);
             for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(vj[i], xc[i]));
@@ -227,7 +230,7 @@ __device__ int cta_jacobi(double2* X, int ldx, int rows, int r, double2* Jm, int
         if (threadIdx.x == 0) *s_flag = 0;
         __syncthreads();
         for (int rho = 0; rho < re - 1; ++rho) {
-            for (int pi = w; pi < half; pi += NW) {
+            for (int pi = w; pi < half; pi += nwarps()) {
                 int i, j;
                 if (pi == 0) {
                     i = rho;
@@ -302,7 +305,7 @@ __device__ void cta_cpqr(double2* A, int ld, int rows, int cols, int extra, int*
                          double rcond, Red& red, int* out_rank, int* out_k, double* out_eps) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int c = threadIdx.x; c < cols; c += blockDim.x) perm[c] = c;
-    for (int c = w; c < cols; c += NW) {
+    for (int c = w; c < cols; c += nwarps()) {
         double s = 0.0;
         for (int i = lane; i < rows; i += 32) s += cabs2(A[(int64_t)c * ld + i]);
         s = warp_sum(s);
@@ -395,10 +398,7 @@ __device__ void cta_backsub(const double2* Rm, int ldr, const double2* diag, int
 // phase 1: fill B | D and A, pivoted QR of B (with D)
 // ----------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(SBT) sbuild_phase1(SBuildJob* jobs, double kappa, double rcond) {
-    __shared__ Red red;
-    extern __shared__ double2 s_v[];
-    SBuildJob& J = jobs[blockIdx.x];
+__device__ __forceinline__ void sbuild_phase1(SBuildJob& J, double kappa, double rcond, Red& red, double2* s_v) {
     fill_kernel_matrix<DIM>(J.BD, J.p, J.z, J.p, J.x, J.m, kappa);
     fill_kernel_matrix<DIM>(J.BD + (int64_t)J.m * J.p, J.p, J.z, J.p, J.y, J.n, kappa);
     fill_kernel_matrix<DIM>(J.AU, J.m, J.x, J.m, J.y, J.n, kappa);
@@ -410,10 +410,7 @@ __global__ void __launch_bounds__(SBT) sbuild_phase1(SBuildJob* jobs, double kap
 // ----------------------------------------------------------------------------
 // phase 2: Z*, C (minimum norm), U, pivoted QR of A (with U)
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(SBT) sbuild_phase2(SBuildJob* jobs, double rcond) {
-    __shared__ Red red;
-    extern __shared__ double2 s_v[];
-    SBuildJob& J = jobs[blockIdx.x];
+__device__ __forceinline__ void sbuild_phase2(SBuildJob& J, double rcond, Red& red, double2* s_v) {
     const int m = J.m, n = J.n, p = J.p, k = J.k, rB = J.rankB;
     // skeleton indices
     for (int i = threadIdx.x; i < k; i += blockDim.x) J.skel[i] = J.permB[i];
@@ -485,10 +482,7 @@ __global__ void __launch_bounds__(SBT) sbuild_phase2(SBuildJob* jobs, double rco
 // phase 3: truncated SVD of A from its pivoted QR (one-sided Jacobi on
 // R_A^H), the factors of A^+, and S
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(SBT) sbuild_phase3(SBuildJob* jobs, double rcond) {
-    __shared__ Red red;
-    __shared__ int s_flag, s_r;
-    SBuildJob& J = jobs[blockIdx.x];
+__device__ __forceinline__ void sbuild_phase3(SBuildJob& J, double rcond, Red& red, int& s_flag, int& s_r) {
     const int m = J.m, n = J.n, k = J.k, rA = J.rankA;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // X = R_A^H (n x rA, ld n) and J = I (rA x rA, ld n)
@@ -509,7 +503,7 @@ __global__ void __launch_bounds__(SBT) sbuild_phase3(SBuildJob* jobs, double rco
     const double tol = 2.220446049250313e-16 * sqrt((double)max(n, 1));
     const int sweeps = cta_jacobi(J.XA, n, n, rA, J.JA, n, tol, 60, &s_flag);
     // singular values = column norms of X J
-    for (int i = w; i < rA; i += NW) {
+    for (int i = w; i < rA; i += nwarps()) {
         double sum = 0.0;
         for (int l = lane; l < n; l += 32) sum += cabs2(J.XA[(int64_t)i * n + l]);
         sum = warp_sum(sum);
@@ -582,6 +576,48 @@ __global__ void __launch_bounds__(SBT) sbuild_phase3(SBuildJob* jobs, double rco
     }
     sq = block_sum(sq, red);
     if (threadIdx.x == 0) J.snorm = sqrt(sq);
+}
+
+// ----------------------------------------------------------------------------
+// persistent launches: every CTA takes the next shape from an atomic counter.
+// The host orders the shapes by decreasing work, so this is longest-
+// processing-time-first scheduling over uneven sizes, and a launch covers the
+// whole batch with a grid sized to the GPU.  The three phases stay separate
+// kernels (one register allocation each; a fused kernel spilled).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int next_job(int* counter, int* s_job) {
+    if (threadIdx.x == 0) *s_job = atomicAdd(counter, 1);
+    __syncthreads();
+    const int j = *s_job;
+    __syncthreads();  // every thread holds j before thread 0 fetches the next one
+    return j;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(SBT_MAX) sbuild_phase1_kernel(SBuildJob* jobs, int njobs, int* counter,
+                                                                double kappa, double rcond) {
+    __shared__ Red red;
+    __shared__ int s_job;
+    extern __shared__ double2 s_v[];
+    for (int j = next_job(counter, &s_job); j < njobs; j = next_job(counter, &s_job))
+        sbuild_phase1<DIM>(jobs[j], kappa, rcond, red, s_v);
+}
+
+__global__ void __launch_bounds__(SBT_MAX) sbuild_phase2_kernel(SBuildJob* jobs, int njobs, int* counter,
+                                                                double rcond) {
+    __shared__ Red red;
+    __shared__ int s_job;
+    extern __shared__ double2 s_v[];
+    for (int j = next_job(counter, &s_job); j < njobs; j = next_job(counter, &s_job))
+        sbuild_phase2(jobs[j], rcond, red, s_v);
+}
+
+__global__ void __launch_bounds__(SBT_MAX) sbuild_phase3_kernel(SBuildJob* jobs, int njobs, int* counter,
+                                                                double rcond) {
+    __shared__ Red red;
+    __shared__ int s_job, s_flag, s_r;
+    for (int j = next_job(counter, &s_job); j < njobs; j = next_job(counter, &s_job))
+        sbuild_phase3(jobs[j], rcond, red, s_flag, s_r);
 }
 
 // ----------------------------------------------------------------------------
@@ -693,31 +729,36 @@ __global__ void __launch_bounds__(256) recon_kernel(const RhsBody* __restrict__ 
     for (int j = threadIdx.x; j < n; j += blockDim.x) qmfs[(int64_t)r * Nm + B.moff + j] = qm[j];
 }
 
-void launch_sbuild_phase1(int dim, SBuildJob* d_jobs, int njobs, int pmax, double kappa,
-                          double rcond, cudaStream_t st) {
-    const size_t sm = (size_t)std::max(pmax, 1) * sizeof(double2);
-    if (dim == 2) {
-        if (sm > 48 * 1024)
-            MBS_CUDA_TRY(cudaFuncSetAttribute(sbuild_phase1<2>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        sbuild_phase1<2><<<njobs, SBT, sm, st>>>(d_jobs, kappa, rcond);
-    } else {
-        if (sm > 48 * 1024)
-            MBS_CUDA_TRY(cudaFuncSetAttribute(sbuild_phase1<3>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        sbuild_phase1<3><<<njobs, SBT, sm, st>>>(d_jobs, kappa, rcond);
-    }
-    MBS_CHECK_LAUNCH();
+template <typename K>
+static int blocks_per_sm(K kern, int threads, size_t sm) {
+    if (sm > 48 * 1024)
+        MBS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int nb = 0;
+    MBS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, sm));
+    return std::max(nb, 1);
 }
 
-void launch_sbuild_phase2(SBuildJob* d_jobs, int njobs, int mmax, double rcond, cudaStream_t st) {
-    const size_t sm = (size_t)std::max(mmax, 1) * sizeof(double2);
-    if (sm > 48 * 1024)
-        MBS_CUDA_TRY(cudaFuncSetAttribute(sbuild_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm));
-    sbuild_phase2<<<njobs, SBT, sm, st>>>(d_jobs, rcond);
+void launch_sbuild(int dim, SBuildJob* d_jobs, int njobs, int* d_counter, int rows_max, int threads,
+                   double kappa, double rcond, cudaStream_t st) {
+    if (njobs == 0) return;
+    if (threads != 128 && threads != 256 && threads != 512)
+        throw MbsError{MBS_ERR_ARG, "S build: threads per CTA must be 128, 256 or 512"};
+    const size_t sm = (size_t)std::max(rows_max, 1) * sizeof(double2);
+    const int nsm = mbs_num_sms();
+    MBS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, 3 * sizeof(int), st));
+    if (dim == 2) {
+        const int g = std::min(njobs, nsm * blocks_per_sm(sbuild_phase1_kernel<2>, threads, sm));
+        sbuild_phase1_kernel<2><<<g, threads, sm, st>>>(d_jobs, njobs, d_counter, kappa, rcond);
+    } else {
+        const int g = std::min(njobs, nsm * blocks_per_sm(sbuild_phase1_kernel<3>, threads, sm));
+        sbuild_phase1_kernel<3><<<g, threads, sm, st>>>(d_jobs, njobs, d_counter, kappa, rcond);
+    }
     MBS_CHECK_LAUNCH();
-    sbuild_phase3<<<njobs, SBT, 0, st>>>(d_jobs, rcond);
+    int g = std::min(njobs, nsm * blocks_per_sm(sbuild_phase2_kernel, threads, sm));
+    sbuild_phase2_kernel<<<g, threads, sm, st>>>(d_jobs, njobs, d_counter + 1, rcond);
+    MBS_CHECK_LAUNCH();
+    g = std::min(njobs, nsm * blocks_per_sm(sbuild_phase3_kernel, threads, 0));
+    sbuild_phase3_kernel<<<g, threads, 0, st>>>(d_jobs, njobs, d_counter + 2, rcond);
     MBS_CHECK_LAUNCH();
 }
 

@@ -57,9 +57,12 @@ struct RhsBody {
     const double2* W;      // injected k x m, or nullptr
 };
 
-void launch_sbuild_phase1(int dim, SBuildJob* d_jobs, int njobs, int pmax, double kappa,
-                          double rcond, cudaStream_t st);
-void launch_sbuild_phase2(SBuildJob* d_jobs, int njobs, int mmax, double rcond, cudaStream_t st);
+// The whole build of njobs shapes: one persistent launch per phase of
+// `threads`-thread CTAs (128, 256 or 512) that take the jobs in order from
+// d_counter (3 ints, one per phase, zeroed here); rows_max = max over the
+// jobs of max(p, m) (shared-memory reflector).
+void launch_sbuild(int dim, SBuildJob* d_jobs, int njobs, int* d_counter, int rows_max, int threads,
+                   double kappa, double rcond, cudaStream_t st);
 void launch_rhs(const RhsBody* d_bodies, int T, int nrhs, int mmax, int nmax, const double2* v,
                 int64_t Mtot, double2* b, int64_t N, cudaStream_t st);
 // q_mfs_tau = A_tau^+ (v_tau - U_tau w_hat_tau) for every body (Sec. 4.6), with
