@@ -90,9 +90,16 @@ def parse():
                     help="steps of the end-to-end (host buffers) measurement")
     ap.add_argument("--fp64-max-iter", type=int, default=8000,
                     help="iteration cap of the measured plain-FP64 solve (config 1)")
-    ap.add_argument("--serve-requests", type=int, default=24,
-                    help="requests of the served trace (0 = skip); body counts scaled to 20..300")
-    ap.add_argument("--serve-tmax", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the served trace at full size (0 = skip serving)")
+    ap.add_argument("--serve-tmax", type=int, default=3000)
+    ap.add_argument("--serve-max-iter", type=int, default=20,
+                    help="inner-iteration cap per served request of the full-size trace")
+    ap.add_argument("--serve-policy", choices=["fifo", "sjf"], default="sjf",
+                    help="admission order of the server: arrival order, or shortest estimated work first")
+    ap.add_argument("--serve-compare", type=int, default=8,
+                    help="requests of the body-count-20..300 trace served by both the mixed and the FP64 "
+                         "path (0 = skip)")
     ap.add_argument("--mac", type=int, default=0,
                     help="FP32 G_hat kernel (mac_path option): 0 auto (tcgen05), 1 FP32 pipe, "
                          "2 mma.sync tensor-core multiply-add, 3 tcgen05 tensor-core multiply-add")
@@ -104,51 +111,93 @@ def parse():
     return ap.parse_args()
 
 
-def run_serving(a, pkg, mi):
-    """Replay a prefix of the serving trace (exponential arrivals at 20/s,
-    2D/3D mix 70/30, kappa ~ U(5, 50), 1..32 right-hand sides) against the
-    continuous-batching server; latency = completion - arrival."""
+def _serve_trace(pkg, mi, trace, tol, slots, policy=0, fp64=False, max_iter=0, log=None):
+    """Replay requests against the continuous-batching server at their arrival
+    times; latency = completion - arrival (submission)."""
     import numpy as np
-    trace = mi.serving_trace(seed=0, n=a.serve_requests, Tmin=20, Tmax=a.serve_tmax)
     work = [(r, mi.request_workload(r)) for r in trace]
     data = [(r, wl, wl.boundary_data()) for r, wl in work]
-    srv = pkg.Server(max_active=4)
+    srv = pkg.Server(max_active=slots)
+    srv.set_policy(policy)
     t0 = time.perf_counter()
     ids = []
     for r, wl, v in data:
         delay = r.arrival - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
-        ids.append((r, srv.submit(wl, v, tol=1e-9)))
+        ids.append((r, srv.submit(wl, v, tol=tol, fp64=fp64, max_iter=max_iter)))
     srv.drain()
-    lat, done, fails = [], [], 0
-    for r, rid in ids:
-        res = srv.poll(rid)
-        if res["done"] != 1:
-            fails += 1
-            continue
-        lat.append(res["t_end"] - res["t_submit"])
-        done.append(res["t_end"])
-    first = min(srv.poll(rid)["t_submit"] for _, rid in ids)
-    lat = np.array(lat)
-    waits, serv = [], []
-    for r, rid in ids:
-        res = srv.poll(rid)
-        if res["done"] == 1:
-            waits.append(res["t_start"] - res["t_submit"])
-            serv.append(res["t_end"] - res["t_start"])
-            print(f"served: rid={r.rid} dim={r.dim} T={r.T} N={res['N']} nrhs={r.nrhs} kappa={r.kappa:.1f} "
-                  f"iterations={res['inner_iterations']} wait_s={waits[-1]:.2f} service_s={serv[-1]:.2f}",
-                  file=sys.stderr)
+    res = [(r, srv.poll(rid)) for r, rid in ids]
     srv.close()
-    return {"requests": len(ids), "failed": fails,
-            "mean_wait_s": float(np.mean(waits)) if waits else None,
-            "mean_service_s": float(np.mean(serv)) if serv else None,
-            "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
-            "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
-            "solves_per_s": len(done) / (max(done) - first) if done else None,
-            "trace": f"first {len(ids)} requests of the seed-0 trace, body counts 20..{a.serve_tmax}, "
-                     "mixed precision to rel. residual 1e-9, 4 concurrent slots"}
+    ok = [(r, x) for r, x in res if x["done"] == 1]
+    lat = np.array([x["t_end"] - x["t_submit"] for _, x in ok])
+    waits = np.array([x["t_start"] - x["t_submit"] for _, x in ok])
+    serv = np.array([x["t_end"] - x["t_start"] for _, x in ok])
+    for r, x in ok:
+        if log is not None:
+            print(f"{log}: rid={r.rid} dim={r.dim} T={r.T} N={x['N']} nrhs={r.nrhs} kappa={r.kappa:.1f} "
+                  f"iterations={x['inner_iterations']} converged={x['converged']} "
+                  f"wait_s={x['t_start'] - x['t_submit']:.2f} service_s={x['t_end'] - x['t_start']:.2f}",
+                  file=sys.stderr)
+    # device-side overlap: the requests' device intervals (events on their own
+    # streams) and their G_hat kernel time
+    iv = sorted((x["dev_start"], x["dev_end"]) for _, x in ok if x["dev_end"] > x["dev_start"])
+    edges = sorted([(s0, 1) for s0, _ in iv] + [(e0, -1) for _, e0 in iv])
+    union = multi = 0.0
+    depth, last = 0, None
+    for t, d in edges:
+        if last is not None and depth >= 1:
+            union += t - last
+            if depth >= 2:
+                multi += t - last
+        depth += d
+        last = t
+    busy = sum(x["g_busy_ms"] for _, x in ok) / 1e3
+    first = min(x["t_submit"] for _, x in res) if res else 0.0
+    done_t = [x["t_end"] for _, x in ok]
+    return {"requests": len(res), "failed": len(res) - len(ok),
+            "converged": int(sum(x["converged"] for _, x in ok)),
+            "mean_wait_s": float(waits.mean()) if len(ok) else None,
+            "mean_service_s": float(serv.mean()) if len(ok) else None,
+            "p50_s": float(np.percentile(lat, 50)) if len(ok) else None,
+            "p99_s": float(np.percentile(lat, 99)) if len(ok) else None,
+            "solves_per_s": len(done_t) / (max(done_t) - first) if done_t else None,
+            "overlap_fraction": multi / union if union > 0 else 0.0,
+            "g_busy_over_device_union": busy / union if union > 0 else None}
+
+
+def run_serving(a, pkg, mi):
+    """The serving trace (exponential arrivals at 20/s, T ~ U{20..3000}, 2D/3D
+    mix 70/30, kappa ~ U(5, 50), 1..32 right-hand sides): the first
+    serve_requests requests at full size under an inner-iteration cap, and,
+    on the same trace with body counts 20..300 so that both paths converge,
+    the mixed and the plain FP64 path to 1e-9."""
+    slots = 4
+    policy = {"fifo": 0, "sjf": 1}[a.serve_policy]
+    trace = mi.serving_trace(seed=0, n=a.serve_requests, Tmin=20, Tmax=a.serve_tmax)
+    full = _serve_trace(pkg, mi, trace, 1e-9, slots, policy=policy, max_iter=a.serve_max_iter,
+                        log="served")
+    full["trace"] = (f"first {len(trace)} requests of the seed-0 trace: arrivals at 20/s, T ~ U{{20..{a.serve_tmax}}}, "
+                     f"2D/3D 70/30, kappa ~ U(5,50), nrhs ~ U{{1..32}}; mixed precision to rel. residual 1e-9 "
+                     f"with at most {a.serve_max_iter} inner iterations per request (time-to-solution capped: "
+                     f"the full trace is hours of GPU work); {slots} slots, admission "
+                     f"{'shortest estimated work first' if policy else 'in arrival order'}")
+    out = {"full_shape": full}
+    if a.serve_compare > 0:
+        small = mi.serving_trace(seed=0, n=a.serve_compare, Tmin=20, Tmax=300)
+        cmp = {}
+        for name, fp64 in (("mixed", False), ("fp64", True)):
+            cmp[name] = _serve_trace(pkg, mi, small, 1e-9, slots, policy=policy, fp64=fp64,
+                                     log=f"served_{name}")
+        out["mixed_vs_fp64"] = {
+            "trace": f"first {len(small)} requests of the seed-0 trace with T ~ U{{20..300}}, solved to 1e-9 "
+                     f"(no cap), {slots} slots, the same arrivals for both paths",
+            "p50_mixed_s": cmp["mixed"]["p50_s"], "p99_mixed_s": cmp["mixed"]["p99_s"],
+            "p50_fp64_s": cmp["fp64"]["p50_s"], "p99_fp64_s": cmp["fp64"]["p99_s"],
+            "mixed": cmp["mixed"], "fp64": cmp["fp64"]}
+    out["p50_s"], out["p99_s"] = full["p50_s"], full["p99_s"]
+    out["overlap_fraction"] = full["overlap_fraction"]
+    return out
 
 
 def run_kernel_only(a):
