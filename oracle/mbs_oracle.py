@@ -8,6 +8,11 @@ What it follows, step by step, in the paper's order and notation:
   phi            fundamental solution phi_kappa                (Sec. 3.1, eq. FundamentalSol)
   cpqr_id        column-pivoted QR of B halted at k or eps,
                  interpolative decomposition B ~ B(:,I) Z*     (Sec. 4.2, eq. B_fac)
+  cpqr_id_sketch the same ID computed from a Gaussian sketch Omega B
+                 (randomized ID of the ID framework the paper
+                 cites for Sec. 4.2; Omega from philox4x32_10 and
+                 gaussian_sketch, a counter-based generator from
+                 its published definition)
   tsvd_solve     backward-stable least squares by truncated SVD (Sec. 3.1; Sec. 4.3-4.4)
   build_shape    S = Z* C A^+ U, W = Z* C A^+                  (Sec. 4.2-4.5, eq. scattering-matrix)
   layout         skeleton points x_hat of every placed body    (Sec. 4.2; reuse of S per shape, Sec. 5.1 Ex. 4)
@@ -37,8 +42,11 @@ Pins (tests, -m "not gpu"): separation-of-variables closed forms for a circle
 MFS on tiny inputs, the ID identities, rigid-motion invariance, and textbook
 values of H0; for the reconstruction, the circle series between Gamma and the
 proxy, the sound-soft condition on Gamma between collocation points (and its
-spectral decay), and agreement of MFS and skeleton sources away from a body.
-No function here is "parity unpinned".
+spectral decay), and agreement of MFS and skeleton sources away from a body;
+for the randomized ID, the generator's published known-answer vectors, the
+moments of the Gaussian sketch, exactness on low-rank matrices, the identity
+sketch reducing to the pivoted-QR ID, and an ID error within a small factor of
+the deterministic one.  No function here is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -49,7 +57,7 @@ import scipy.linalg as sla
 from scipy.special import hankel1
 
 __all__ = [
-    "phi", "kernel_matrix", "cpqr_id", "tsvd_solve", "tsvd_pinv", "build_shape", "build_all",
+    "phi", "kernel_matrix", "cpqr_id", "cpqr_id_sketch", "philox4x32_10", "gaussian_sketch", "tsvd_solve", "tsvd_pinv", "build_shape", "build_all",
     "layout", "apply_W", "G_dense", "G_matvec", "G_rows", "apply_operator", "rhs", "solve_dense", "gmres",
     "field", "solve_workload", "incoming_on_boundary", "reconstruct_mfs", "field_near",
     "proxy_body",
@@ -137,6 +145,63 @@ def cpqr_id(B: np.ndarray, k: int = 0, eps: float = 0.0, tie_tol: float = TIE_TO
 
 
 # ----------------------------------------------------------------------------
+# Randomized ID: the skeleton from a Gaussian sketch of B
+# ----------------------------------------------------------------------------
+_PHILOX_M = (0xD2511F53, 0xCD9E8D57)
+_PHILOX_W = (0x9E3779B9, 0xBB67AE85)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11): ctr is
+    (..., 4) and key (..., 2), unsigned 32-bit; returns (..., 4) uint32.  Each
+    round multiplies counter words 0 and 2 by the two constants, swaps and
+    xors the high halves with the other words and the key; the key is bumped
+    by the two Weyl constants between rounds."""
+    c = [np.asarray(ctr[..., i], dtype=np.uint64) for i in range(4)]
+    k0 = np.asarray(key[..., 0], dtype=np.uint64)
+    k1 = np.asarray(key[..., 1], dtype=np.uint64)
+    m32 = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + np.uint64(_PHILOX_W[0])) & m32
+            k1 = (k1 + np.uint64(_PHILOX_W[1])) & m32
+        p0 = np.uint64(_PHILOX_M[0]) * c[0]
+        p1 = np.uint64(_PHILOX_M[1]) * c[2]
+        c = [(p1 >> np.uint64(32)) ^ c[1] ^ k0, p1 & m32, (p0 >> np.uint64(32)) ^ c[3] ^ k1, p0 & m32]
+    return np.stack(c, axis=-1).astype(np.uint32)
+
+
+def gaussian_sketch(d: int, p: int, seed: int, shape_index: int) -> np.ndarray:
+    """d x p complex Gaussian test matrix (unit variance: real and imaginary
+    parts N(0, 1/2)).  Entry (i, l) takes counter (l, i, 0, 0) and key
+    (seed, shape_index); the four output words give two 53-bit uniforms
+    u = (w_a 2^21 + floor(w_b / 2^11) + 1/2) 2^-53 in (0, 1), and the
+    Box-Muller transform gives sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2)."""
+    ii, ll = np.meshgrid(np.arange(d), np.arange(p), indexing="ij")
+    ctr = np.stack([ll, ii, np.zeros_like(ii), np.zeros_like(ii)], axis=-1).astype(np.uint64)
+    key = np.empty(ii.shape + (2,), dtype=np.uint64)
+    key[..., 0] = seed & 0xFFFFFFFF
+    key[..., 1] = shape_index & 0xFFFFFFFF
+    w = philox4x32_10(ctr, key).astype(np.uint64)
+    two53 = 2.0 ** -53
+    u1 = ((w[..., 0] << np.uint64(21)) + (w[..., 1] >> np.uint64(11))).astype(np.float64) * two53 + 0.5 * two53
+    u2 = ((w[..., 2] << np.uint64(21)) + (w[..., 3] >> np.uint64(11))).astype(np.float64) * two53 + 0.5 * two53
+    rad = np.sqrt(-2.0 * np.log(u1))
+    th = 2.0 * math.pi * u2
+    return (rad * np.cos(th) + 1j * rad * np.sin(th)) / math.sqrt(2.0)
+
+
+def cpqr_id_sketch(B: np.ndarray, k: int, Omega: np.ndarray, tie_tol: float = TIE_TOL):
+    """Randomized interpolative decomposition: the column-pivoted QR of the
+    sketch Y = Omega B (d x m, d >= k rows, Omega a Gaussian test matrix),
+    halted at k, gives the skeleton I_hat and Z* = [I | R11^{-1} R12] of Y,
+    which is also an ID of B: B ~ B(:, I_hat) Z* (the columns of Y are the
+    columns of B seen through Omega, so a column subset that spans Y's
+    columns spans B's to about the same error).  Returns what cpqr_id does."""
+    return cpqr_id(Omega @ B, k=k, tie_tol=tie_tol)
+
+
+# ----------------------------------------------------------------------------
 # Sec. 3.1 / 4.3 / 4.4: backward-stable least squares (truncated SVD)
 # ----------------------------------------------------------------------------
 def _tsvd(A: np.ndarray, rcond: float = LS_RCOND):
@@ -162,14 +227,19 @@ def tsvd_pinv(A: np.ndarray, rcond: float = LS_RCOND) -> np.ndarray:
 # Sec. 4.2-4.5: the local scattering matrix of one shape
 # ----------------------------------------------------------------------------
 def build_shape(dim: int, kappa: float, x, y, z, k: int = 0, eps: float = 0.0,
-                rcond: float = LS_RCOND) -> dict:
+                rcond: float = LS_RCOND, sketch=None) -> dict:
     """S = Z* C A^+ U (k x k) and W = Z* C A^+ (k x m) for one shape.
 
     B(i,j) = phi(z_i - x_j) (p x m, eq. B-matrix); CPQR/ID of B gives I_hat and Z*;
     U = conj(Z) = (Z*)^T (Sec. 4.2); A(i,j) = phi(x_i - y_j) (m x n, Sec. 4.3);
     D(i,j) = phi(z_i - y_j) (p x n) and C solves B C = D (Sec. 4.4)."""
     B = kernel_matrix(dim, kappa, z, x)
-    skel, Zs, perm, R, eps_ach = cpqr_id(B, k=k, eps=eps)
+    if sketch is not None and k > 0 and k + sketch[2] < B.shape[0]:
+        # randomized ID: sketch = (seed, shape index, oversampling)
+        Omega = gaussian_sketch(k + sketch[2], B.shape[0], sketch[0], sketch[1])
+        skel, Zs, perm, R, eps_ach = cpqr_id_sketch(B, k, Omega)
+    else:
+        skel, Zs, perm, R, eps_ach = cpqr_id(B, k=k, eps=eps)
     A = kernel_matrix(dim, kappa, x, y)
     D = kernel_matrix(dim, kappa, z, y)
     C = tsvd_solve(B, D, rcond)
@@ -190,13 +260,15 @@ def build_shape(dim: int, kappa: float, x, y, z, k: int = 0, eps: float = 0.0,
             "A_svd": (Ua, sa, Vh), "eps": eps_ach, "k": len(skel)}
 
 
-def build_all(wl) -> list:
-    """Scattering data for every distinct shape of a workload (reuse per shape, Sec. 5.1 Ex. 4)."""
+def build_all(wl, sketch=None) -> list:
+    """Scattering data for every distinct shape of a workload (reuse per shape, Sec. 5.1 Ex. 4).
+    sketch = (seed, oversampling) selects the randomized ID for fixed-k shapes."""
     used = sorted(set(int(s) for s in wl.body_shape))
     out = [None] * len(wl.shapes)
     for s in used:
         sh = wl.shapes[s]
-        out[s] = build_shape(wl.dim, wl.kappa, sh.x, sh.y, sh.z, k=sh.k, eps=sh.eps)
+        sk = None if sketch is None else (sketch[0], s, sketch[1])
+        out[s] = build_shape(wl.dim, wl.kappa, sh.x, sh.y, sh.z, k=sh.k, eps=sh.eps, sketch=sk)
     return out
 
 
@@ -436,9 +508,10 @@ def field_near(wl, sdata, lay, qhat, qmfs, targets) -> np.ndarray:
     return out
 
 
-def solve_workload(wl, method: str = "auto", tol: float = 1e-13):
-    """Full oracle pipeline: S per shape, layout, b = W v, solve.  Returns a dict."""
-    sdata = build_all(wl)
+def solve_workload(wl, method: str = "auto", tol: float = 1e-13, sketch=None):
+    """Full oracle pipeline: S per shape, layout, b = W v, solve.  Returns a dict.
+    sketch = (seed, oversampling): randomized ID (see build_all)."""
+    sdata = build_all(wl, sketch=sketch)
     lay = layout(wl, sdata)
     v = wl.boundary_data()
     b = rhs(wl, sdata, lay, v)

@@ -458,3 +458,69 @@ def test_near_field_sphere_closed_form_converges():
         assert np.all(orc.proxy_body(wl, tg) == 0)
         errs.append(_relerr(orc.field_near(wl, res["sdata"], res["layout"], res["q"], qm, tg)[:, 0], ue))
     assert errs[-1] < 1e-5 and errs[1] < 0.3 * errs[0] and errs[2] < 0.3 * errs[1], errs
+
+
+# --------------------------------------------------------------------------
+# randomized ID (Gaussian sketch; the ID framework the paper cites for Sec. 4.2)
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    """philox4x32_10 reproduces the generator's published known-answer vectors."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = orc.philox4x32_10(np.array(v[:4], dtype=np.uint64), np.array(v[4:6], dtype=np.uint64))
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_gaussian_sketch_moments_and_streams():
+    """Complex standard normal entries (E z = 0, E |z|^2 = 1, E z^2 = 0, real
+    part Gaussian by its fourth moment), different streams per shape index and
+    seed, and the same matrix on every call."""
+    O = orc.gaussian_sketch(400, 500, 11, 2)
+    n = O.size
+    assert abs(O.mean()) < 5 / math.sqrt(n)
+    assert abs(np.mean(np.abs(O) ** 2) - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert abs(np.mean(O ** 2)) < 5 / math.sqrt(n)
+    x = math.sqrt(2.0) * O.real.ravel()
+    assert abs(np.mean(x ** 4) - 3.0) < 0.05
+    assert np.array_equal(O, orc.gaussian_sketch(400, 500, 11, 2))
+    assert not np.allclose(O[:10, :10], orc.gaussian_sketch(400, 500, 11, 3)[:10, :10])
+    assert not np.allclose(O[:10, :10], orc.gaussian_sketch(400, 500, 12, 2)[:10, :10])
+
+
+def test_sketch_id_is_exact_on_low_rank_and_identity_sketch_is_cpqr():
+    """For B of exact rank r <= k the sketch ID reproduces B to rounding; with
+    Omega = I the sketch ID is the deterministic pivoted-QR ID."""
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(90, 20)) + 1j * rng.normal(size=(90, 20))
+    Y = rng.normal(size=(20, 70)) + 1j * rng.normal(size=(20, 70))
+    B = X @ Y
+    skel, Zs, *_ = orc.cpqr_id_sketch(B, 20, orc.gaussian_sketch(30, 90, 5, 0))
+    assert np.linalg.norm(B - B[:, skel] @ Zs) <= 1e-12 * np.linalg.norm(B)
+    B2 = rng.normal(size=(40, 30)) + 1j * rng.normal(size=(40, 30))
+    a = orc.cpqr_id(B2, k=12)
+    b = orc.cpqr_id_sketch(B2, 12, np.eye(40))
+    assert np.array_equal(a[0], b[0]) and np.allclose(a[1], b[1], rtol=0, atol=1e-13)
+
+
+def test_sketch_id_error_close_to_deterministic_on_an_mfs_shape():
+    """On the 10-body workload's shape (B 129 x 128, k = 64 where B's singular
+    values have fallen to 5.6e-6 of the largest) the sketch ID with 10 extra
+    rows approximates B within 10x of the deterministic ID's error; the
+    solve's field moves by about that ID error."""
+    wl = mi.config0()
+    sh = wl.shapes[0]
+    B = orc.kernel_matrix(2, wl.kappa, sh.z, sh.x)
+    sk, Zs, *_ = orc.cpqr_id(B, k=sh.k)
+    e_det = np.linalg.norm(B - B[:, sk] @ Zs) / np.linalg.norm(B)
+    sk2, Zs2, *_ = orc.cpqr_id_sketch(B, sh.k, orc.gaussian_sketch(sh.k + 10, B.shape[0], 7, 0))
+    e_sk = np.linalg.norm(B - B[:, sk2] @ Zs2) / np.linalg.norm(B)
+    assert e_sk <= 10 * e_det
+    assert np.array_equal(Zs2[:, sk2], np.eye(sh.k))
+    ref = orc.solve_workload(wl)
+    rs = orc.solve_workload(wl, sketch=(7, 10))
+    tg = mi.far_targets(wl, 64, mode="ring")
+    u0 = orc.field(2, wl.kappa, tg, ref["layout"]["xhat"], ref["q"])
+    u1 = orc.field(2, wl.kappa, tg, rs["layout"]["xhat"], rs["q"])
+    assert np.max(np.abs(u1 - u0)) / np.max(np.abs(u0)) < 10 * max(e_det, e_sk)
