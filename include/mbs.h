@@ -92,6 +92,12 @@ typedef struct mbs_options {
     int sbuild_threads;  /* threads per CTA of the S build (128, 256 or 512); 0 (default): 256 (the build
                             is FP64-pipe-bound: the three sizes measured within 2 % on GB300); -1: tuned on the
                             first build of a size class (when autotune is on), at the cost of ~half a build */
+    int id_sketch;       /* randomized ID (Sec. 4.2, the ID framework the paper cites): > 0 takes the
+                            skeleton and Z* of each fixed-k shape from the pivoted QR of the sketch
+                            Omega B with k + id_sketch rows (Omega complex Gaussian from Philox4x32-10,
+                            key (id_seed, shape index)), when that is fewer than B's p rows; 0 (default):
+                            the pivoted QR of B itself */
+    unsigned int id_seed; /* generator key of the sketch */
 } mbs_options;
 
 typedef struct mbs_shape {

@@ -23,7 +23,7 @@ class mbs_options(C.Structure):
         ("ls_rcond", C.c_double), ("stream", C.c_void_p), ("hbm_budget", C.c_size_t),
         ("tile_override", C.c_int), ("block_krylov", C.c_int), ("mac_path", C.c_int),
         ("autotune", C.c_int), ("cuda_graphs", C.c_int), ("fp64_kernel", C.c_int),
-        ("sbuild_threads", C.c_int),
+        ("sbuild_threads", C.c_int), ("id_sketch", C.c_int), ("id_seed", C.c_uint),
     ]
 
 

@@ -1153,6 +1153,7 @@ void validate_options(const mbs_options& o) {
     if (o.sbuild_threads != 0 && o.sbuild_threads != -1 && o.sbuild_threads != 128 && o.sbuild_threads != 256 &&
         o.sbuild_threads != 512)
         throw MbsError{MBS_ERR_ARG, "sbuild_threads must be 0, -1, 128, 256 or 512"};
+    if (o.id_sketch < 0) throw MbsError{MBS_ERR_ARG, "id_sketch must be >= 0"};
 }
 
 template <typename F>
@@ -1516,7 +1517,10 @@ void build(mbs_ctx* c, int nshapes, const mbs_shape* shapes, int nbodies, const 
             const int kcap = s.kfix > 0 ? s.kfix : std::min(s.m, s.p);
             const size_t need = sizeof(double2) * ((size_t)s.p * (s.m + s.n) + (size_t)kcap * std::max(s.m, s.n) +
                                                    (size_t)std::min(s.p, s.m) * (s.n + s.m + 1) +
-                                                   (size_t)s.m * s.n + (size_t)s.n * s.n + s.p + 2 * s.m);
+                                                   (size_t)s.m * s.n + (size_t)s.n * s.n + s.p + 2 * s.m) +
+                                (c->opt.id_sketch > 0 && s.kfix > 0
+                                     ? sizeof(double2) * (size_t)(s.kfix + c->opt.id_sketch) * (s.p + s.m + 1)
+                                     : 0);
             if (!batch.empty() && ws + need > ws_budget) break;
             batch.push_back(used[pos++]);
             ws += need;
@@ -1540,6 +1544,16 @@ void build(mbs_ctx* c, int nshapes, const mbs_shape* shapes, int nbodies, const 
             J.p = s.p;
             J.kfix = s.kfix;
             J.eps = s.eps;
+            const int dsk = s.kfix + c->opt.id_sketch;
+            J.sketch_d = (c->opt.id_sketch > 0 && s.kfix > 0 && dsk < s.p) ? dsk : 0;
+            J.seed = c->opt.id_seed;
+            J.shape_index = batch[j];
+            if (J.sketch_d > 0) {
+                J.OM = (double2*)talloc(sizeof(double2) * (size_t)J.sketch_d * s.p);
+                J.Y = (double2*)talloc(sizeof(double2) * (size_t)J.sketch_d * s.m);
+                J.permY = (int*)talloc(sizeof(int) * s.m);
+                J.diagY = (double2*)talloc(sizeof(double2) * std::min(J.sketch_d, s.m));
+            }
             s.dx = galloc<double>(c, s.x.size());
             s.dy = galloc<double>(c, s.y.size());
             s.dz = galloc<double>(c, s.z.size());
@@ -1638,6 +1652,8 @@ void mbs_default_options(mbs_options* o) {
     o->cuda_graphs = 1;
     o->fp64_kernel = 2;
     o->sbuild_threads = 0;
+    o->id_sketch = 0;
+    o->id_seed = 0;
 }
 
 mbs_status mbs_create(int dim, double kappa, const mbs_options* opt, mbs_ctx** out) {

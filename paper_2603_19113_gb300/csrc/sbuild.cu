@@ -13,6 +13,11 @@
 //            most eps times the largest initial one; the factorisation goes on
 //            to the numerical rank r_B (relative ls_rcond) for the
 //            least-squares solve below.
+//            Randomized ID (option id_sketch): the skeleton and Z* come instead
+//            from the pivoted QR of the sketch Y = Omega B (k + oversampling
+//            rows, Omega a complex Gaussian test matrix from Philox4x32-10
+//            keyed by the seed and the shape index, Box-Muller); B's own
+//            pivoted QR then serves the least-squares solve for C only.
 //  phase 2   Z* = [I_k | R11^{-1} R12] in pivot order (ID, eq. B_fac);
 //            C = minimum-norm least-squares solution of B C = D on the rank r_B
 //            of that factorisation (Sec. 4.4): a complete orthogonal
@@ -397,12 +402,63 @@ __device__ void cta_backsub(const double2* Rm, int ldr, const double2* diag, int
 // ----------------------------------------------------------------------------
 // phase 1: fill B | D and A, pivoted QR of B (with D)
 // ----------------------------------------------------------------------------
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Entry (i, l) of the complex Gaussian test matrix: counter (l, i, 0, 0), key
+// (seed, shape); two 53-bit uniforms in (0, 1) and the Box-Muller transform,
+// scaled to unit variance (the same definition as the oracle's).
+__device__ __forceinline__ double2 sketch_entry(int i, int l, unsigned seed, int shape) {
+    const uint4 w = philox4x32_10(make_uint4((unsigned)l, (unsigned)i, 0u, 0u), make_uint2(seed, (unsigned)shape));
+    const double u1 = (double)(((unsigned long long)w.x << 21) + (w.y >> 11)) * 0x1p-53 + 0x1p-54;
+    const double u2 = (double)(((unsigned long long)w.z << 21) + (w.w >> 11)) * 0x1p-53 + 0x1p-54;
+    const double rad = sqrt(-2.0 * log(u1));
+    const double th = 6.283185307179586 * u2;
+    const double is2 = 0.70710678118654752440;
+    return make_double2(rad * cos(th) * is2, rad * sin(th) * is2);
+}
+
 template <int DIM>
 __device__ __forceinline__ void sbuild_phase1(SBuildJob& J, double kappa, double rcond, Red& red, double2* s_v) {
     fill_kernel_matrix<DIM>(J.BD, J.p, J.z, J.p, J.x, J.m, kappa);
     fill_kernel_matrix<DIM>(J.BD + (int64_t)J.m * J.p, J.p, J.z, J.p, J.y, J.n, kappa);
     fill_kernel_matrix<DIM>(J.AU, J.m, J.x, J.m, J.y, J.n, kappa);
     __syncthreads();
+    if (J.sketch_d > 0) {
+        const int d = J.sketch_d, p = J.p, m = J.m;
+        for (int64_t e = threadIdx.x; e < (int64_t)d * p; e += blockDim.x)
+            J.OM[e] = sketch_entry((int)(e % d), (int)(e / d), J.seed, J.shape_index);
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)d * m; e += blockDim.x) {
+            const int i = (int)(e % d), j = (int)(e / d);
+            double2 sum = make_double2(0.0, 0.0);
+            for (int l = 0; l < p; ++l) sum = cadd(sum, cmul(J.OM[(int64_t)l * d + i], J.BD[(int64_t)j * p + l]));
+            J.Y[e] = sum;
+        }
+        __syncthreads();
+        // the ID from the sketch: halted at k (a cutoff above every column norm)
+        int rankY;
+        cta_cpqr(J.Y, d, d, m, 0, J.permY, J.diagY, J.nrm2, s_v, J.kfix, 0.0, 2.0, red, &rankY, &J.k,
+                 &J.eps_ach);
+        // B's own factorisation, for the least-squares solve of C
+        int kd;
+        double ed;
+        cta_cpqr(J.BD, J.p, J.p, J.m, J.n, J.permB, J.diagB, J.nrm2, s_v, J.kfix, J.eps, rcond, red,
+                 &J.rankB, &kd, &ed);
+        return;
+    }
     cta_cpqr(J.BD, J.p, J.p, J.m, J.n, J.permB, J.diagB, J.nrm2, s_v, J.kfix, J.eps, rcond, red,
              &J.rankB, &J.k, &J.eps_ach);
 }
@@ -412,18 +468,24 @@ __device__ __forceinline__ void sbuild_phase1(SBuildJob& J, double kappa, double
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void sbuild_phase2(SBuildJob& J, double rcond, Red& red, double2* s_v) {
     const int m = J.m, n = J.n, p = J.p, k = J.k, rB = J.rankB;
+    // the ID's factorisation: B's own pivoted QR, or the sketch's
+    const bool sk = J.sketch_d > 0;
+    const double2* RI = sk ? J.Y : J.BD;
+    const int ldi = sk ? J.sketch_d : p;
+    const int* permI = sk ? J.permY : J.permB;
+    const double2* diagI = sk ? J.diagY : J.diagB;
     // skeleton indices
-    for (int i = threadIdx.x; i < k; i += blockDim.x) J.skel[i] = J.permB[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) J.skel[i] = permI[i];
     // Z* (k x m, ld k): identity on the skeleton, T = R11^{-1} R12 elsewhere
     for (int64_t e = threadIdx.x; e < (int64_t)k * m; e += blockDim.x) J.Zs[e] = make_double2(0.0, 0.0);
     __syncthreads();
     for (int i = threadIdx.x; i < k; i += blockDim.x)
-        J.Zs[(int64_t)J.permB[i] * k + i] = make_double2(1.0, 0.0);
+        J.Zs[(int64_t)permI[i] * k + i] = make_double2(1.0, 0.0);
     // T columns: solve into the work area W1 (k x (m-k), ld k)
-    cta_backsub(J.BD, p, J.diagB, k, J.BD + (int64_t)k * p, p, m - k, J.W1, k);
+    cta_backsub(RI, ldi, diagI, k, RI + (int64_t)k * ldi, ldi, m - k, J.W1, k);
     for (int64_t e = threadIdx.x; e < (int64_t)k * (m - k); e += blockDim.x) {
         const int i = (int)(e % k), c = (int)(e / k);
-        J.Zs[(int64_t)J.permB[k + c] * k + i] = J.W1[e];
+        J.Zs[(int64_t)permI[k + c] * k + i] = J.W1[e];
     }
     // C (m x n, ld m): minimum-norm solution of R_B(0:rB, :) (C P_B) = (Q_B^H D)(0:rB, :).
     // X_B = R_B^H (m x rB, ld m), then X_B = Zq Rz (unpivoted QR), so that

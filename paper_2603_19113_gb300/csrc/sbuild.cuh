@@ -12,6 +12,14 @@ struct SBuildJob {
     const double* z;
     int kfix;       // > 0: fixed skeleton count
     double eps;     // else: relative stopping tolerance
+    // randomized ID (0 rows: the ID comes from the pivoted QR of B itself)
+    int sketch_d;        // rows of the Gaussian sketch Omega B (k + oversampling)
+    unsigned int seed;   // generator key: (seed, shape index)
+    int shape_index;
+    double2* OM;         // sketch_d x p: Omega
+    double2* Y;          // sketch_d x m: Omega B, factored in place
+    int* permY;          // m
+    double2* diagY;      // min(sketch_d, m)
     // workspace
     double2* BD;    // p x (m + n), ld p: B | D, factored in place
     double2* AU;    // m x (n + kcap), ld m: A | U, factored in place (kept: A's reflectors)

@@ -586,3 +586,62 @@ def test_single_body_has_no_coupling(pkg):
     b = ctx.rhs(wl.boundary_data())
     x, info = ctx.solve(b)
     assert _rel(x, b) < 1e-14
+
+
+def test_bench_workload_solution_residual_against_oracle_rows(pkg):
+    """The bench's headline solve (1000 bodies, N = 64,000, 8 plane waves, mixed
+    precision to 1e-11, GPU-built S) checked independently of the GPU's own
+    operator: for four sampled bodies, the oracle's G_hat rows applied to the
+    GPU's q_hat, then each body's S (as built), give the residual
+    b - (q + S G q) on those 256 rows.  Bound: 1e-9 relative to |b| on the
+    sampled rows (the solve reached 6e-12 with the GPU operator; the oracle's
+    FP64 rows differ from the GPU's double-float ones by ~1e-13 relative,
+    times ||S|| ~ 25)."""
+    wl = mi.config1()
+    ctx = pkg.Context(2, wl.kappa, precision=pkg.PREC_MIXED, tol=1e-11, restart=200, inner_tol=1e-4,
+                      max_iter=50000, max_sweeps=12)
+    ctx.build_scattering_matrices(wl)
+    b = ctx.rhs(wl.boundary_data())
+    q, info = ctx.solve(b)
+    assert info["rel_residual"] <= 1e-11
+    N, off, xyz = ctx.get_layout()
+    body = np.repeat(np.arange(wl.T), np.diff(off))
+    rng = np.random.default_rng(7)
+    for t in rng.choice(wl.T, 4, replace=False):
+        rows = np.arange(off[t], off[t + 1])
+        Gq = orc.G_rows(2, wl.kappa, xyz, body, q, rows)
+        S = ctx.get_shape(int(wl.body_shape[t]))["S"]
+        r = b[rows] - q[rows] - S @ Gq
+        assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(b[rows]), t
+    ctx.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gpu_randomized_id_matches_oracle_sketch(pkg, dim):
+    """Randomized ID (id_sketch): the GPU generates the same Gaussian sketch as
+    the oracle (Philox4x32-10 keyed by seed and shape, Box-Muller), takes the
+    skeleton from the pivoted QR of Omega B, and builds S from it.  The
+    skeleton equals the oracle's sketch skeleton (and differs from the
+    deterministic one, so the option is in effect); FP64 and mixed solves
+    match the oracle's sketched pipeline in the far field to 1e-9.  2D: the
+    10-body workload (B 129 x 128, k = 64, 74-row sketch); 3D: five
+    ellipsoids (B 141 x 140, k = 70, 80-row sketch)."""
+    wl = mi.config0() if dim == 2 else mi.tiny_3d(seed=0, T=5, kappa=3.0, nth=10, nph=14, p=141, k=70)
+    ref = orc.solve_workload(wl, sketch=(7, 10))
+    det = orc.build_all(wl)
+    tg = mi.far_targets(wl, 96, mode="ring")
+    u_ref = orc.field(dim, wl.kappa, tg, ref["layout"]["xhat"], ref["q"])
+    differs = False
+    for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
+        ctx = pkg.Context(dim, wl.kappa, precision=prec, tol=1e-12, id_sketch=10, id_seed=7)
+        ctx.build_scattering_matrices(wl)
+        for s, sd in enumerate(ref["sdata"]):
+            if sd is None:
+                continue
+            g = np.sort(ctx.get_shape(s)["skel"])
+            assert np.array_equal(g, np.sort(sd["skel"])), s
+            differs = differs or not np.array_equal(g, np.sort(det[s]["skel"]))
+        q, info = ctx.solve(ctx.rhs(ref["v"]))
+        assert _rel(ctx.evaluate_field(tg, q), u_ref) < 1e-9, prec
+        ctx.close()
+    assert differs
