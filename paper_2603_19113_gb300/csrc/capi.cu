@@ -1570,7 +1570,6 @@ void build(mbs_ctx* c, int nshapes, const mbs_shape* shapes, int nbodies, const 
             J.W2 = (double2*)talloc(sizeof(double2) * (size_t)std::min(s.p, s.m) * s.n);
             J.W3 = (double2*)talloc(sizeof(double2) * (size_t)s.m * s.n);
             J.XB = (double2*)talloc(sizeof(double2) * (size_t)s.m * std::min(s.p, s.m));
-            J.diagZ = (double2*)talloc(sizeof(double2) * std::min(s.p, s.m));
             J.XA = (double2*)talloc(sizeof(double2) * (size_t)s.n * s.n);
             J.sig = (double*)talloc(sizeof(double) * s.n);
             J.keep = (int*)talloc(sizeof(int) * s.n);

@@ -11,8 +11,8 @@
 //            same reflectors applied to D.  The skeleton count k is fixed or
 //            the first step at which the largest remaining column norm is at
 //            most eps times the largest initial one; the factorisation goes on
-//            to the numerical rank r_B (relative ls_rcond) for the
-//            least-squares solve below.
+//            to the numerical rank r_B (largest remaining column norm above
+//            10 ls_rcond, see B_QR_CUT) for the least-squares solve below.
 //            Randomized ID (option id_sketch): the skeleton and Z* come instead
 //            from the pivoted QR of the sketch Y = Omega B (k + oversampling
 //            rows, Omega a complex Gaussian test matrix from Philox4x32-10
@@ -21,8 +21,9 @@
 //  phase 2   Z* = [I_k | R11^{-1} R12] in pivot order (ID, eq. B_fac);
 //            C = minimum-norm least-squares solution of B C = D on the rank r_B
 //            of that factorisation (Sec. 4.4): a complete orthogonal
-//            decomposition R_B = Rz^H Zq^H from the QR of R_B^H, then
-//            C P_B = Zq Rz^{-H} (Q_B^H D)(1:r_B, :);
+//            decomposition R_B Z^H = [T 0] by reflectors from the right (RZ
+//            reduction of the trapezoidal R_B), then
+//            C P_B = Z^H [T^{-1} (Q_B^H D)(1:r_B, :); 0];
 //            U = (Z*)^T (Sec. 4.2) and the pivoted QR of A with its reflectors
 //            applied to U, run to the rounding level (0.01 ls_rcond).
 //  phase 3   truncated SVD of A (Sec. 3.1, "truncated SVD"): one-sided Jacobi
@@ -53,6 +54,13 @@ namespace {
 constexpr int SBT_MAX = 512;      // largest CTA size (threads per shape CTA: 128, 256 or 512)
 constexpr int NW_MAX = SBT_MAX / 32;
 constexpr double TIE = 1e-10;
+// The rank of B for the least-squares solve of C: the pivoted QR stops where
+// its largest remaining column norm falls to B_QR_CUT * ls_rcond.  A pivoted
+// QR's diagonal overestimates the singular values it tracks; cut at 10 x
+// ls_rcond it keeps the rank of the truncated SVD at ls_rcond to within 0-2
+// on the test shapes (2D smooth, corner-refined and 3D), where a cut at
+// ls_rcond itself keeps 4-11 more, noise-level directions.
+constexpr double B_QR_CUT = 10.0;
 
 // warps of the CTA (the block size is chosen at launch)
 __device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
@@ -188,34 +196,6 @@ __device__ void householder_step(double2* A, int ld, int rows, int j, int ncols,
         }
     }
     __syncthreads();
-}
-
-// Unpivoted Householder QR of the rows x cols matrix A (leading dimension ld),
-// same storage as householder_step: reflectors on and below the diagonal,
-// R above it and its diagonal in diag.
-__device__ void cta_qr(double2* A, int ld, int rows, int cols, double2* diag, double2* s_v,
-                       Red& red) {
-    const int kmax = min(rows, cols);
-    for (int j = 0; j < kmax; ++j) householder_step(A, ld, rows, j, cols, cols, diag, nullptr, s_v, red);
-}
-
-// X <- H_0 H_1 ... H_{nref-1} X for the reflectors stored in the columns of V
-// (v_j in rows j..rows-1 of column j, leading dimension ldv): the orthogonal
-// factor of a QR applied to the rows x ncols matrix X (leading dimension ldx).
-__device__ void cta_apply_q(const double2* V, int ldv, int rows, int nref, double2* X, int ldx,
-                            int ncols) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = nref - 1; j >= 0; --j) {
-        const double2* vj = V + (int64_t)j * ldv;
-        for (int c = w; c < ncols; c += nwarps()) {
-            double2* xc = X + (int64_t)c * ldx;
-            double2 d = make_double2(0.0, 0.0);
-            for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(vj[i], xc[i]));
-            d = cscale(warp_sum2(d), 2.0);
-            for (int i = j + lane; i < rows; i += 32) xc[i] = csub(xc[i], cmul(vj[i], d));
-        }
-        __syncthreads();
-    }
 }
 
 // One-sided Jacobi (Hestenes 1958) on the r columns of X (rows x r, leading
@@ -455,11 +435,11 @@ __device__ __forceinline__ void sbuild_phase1(SBuildJob& J, double kappa, double
         // B's own factorisation, for the least-squares solve of C
         int kd;
         double ed;
-        cta_cpqr(J.BD, J.p, J.p, J.m, J.n, J.permB, J.diagB, J.nrm2, s_v, J.kfix, J.eps, rcond, red,
+        cta_cpqr(J.BD, J.p, J.p, J.m, J.n, J.permB, J.diagB, J.nrm2, s_v, J.kfix, J.eps, B_QR_CUT * rcond, red,
                  &J.rankB, &kd, &ed);
         return;
     }
-    cta_cpqr(J.BD, J.p, J.p, J.m, J.n, J.permB, J.diagB, J.nrm2, s_v, J.kfix, J.eps, rcond, red,
+    cta_cpqr(J.BD, J.p, J.p, J.m, J.n, J.permB, J.diagB, J.nrm2, s_v, J.kfix, J.eps, B_QR_CUT * rcond, red,
              &J.rankB, &J.k, &J.eps_ach);
 }
 
@@ -487,39 +467,87 @@ __device__ __forceinline__ void sbuild_phase2(SBuildJob& J, double rcond, Red& r
         const int i = (int)(e % k), c = (int)(e / k);
         J.Zs[(int64_t)permI[k + c] * k + i] = J.W1[e];
     }
-    // C (m x n, ld m): minimum-norm solution of R_B(0:rB, :) (C P_B) = (Q_B^H D)(0:rB, :).
-    // X_B = R_B^H (m x rB, ld m), then X_B = Zq Rz (unpivoted QR), so that
-    // R_B = Rz^H Zq^H and C P_B = Zq Rz^{-H} (Q_B^H D)(0:rB, :).
-    for (int64_t e = threadIdx.x; e < (int64_t)m * rB; e += blockDim.x) {
-        const int c = (int)(e % m), i = (int)(e / m);
-        double2 v = make_double2(0.0, 0.0);
-        if (c == i)
-            v = J.diagB[i];
-        else if (c > i)
-            v = J.BD[(int64_t)c * p + i];
-        J.XB[e] = make_double2(v.x, -v.y);
-    }
-    __syncthreads();
-    cta_qr(J.XB, m, m, rB, J.diagZ, s_v, red);
-    // Y = Rz^{-H} (Q_B^H D)(0:rB, :) by forward substitution (Rz^H is lower
-    // triangular), one thread per column, into W2 (rB x n, ld rB)
-    const int ldy = rB > 0 ? rB : 1;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int i = 0; i < rB; ++i) {
-            double2 sum = J.BD[(int64_t)(m + c) * p + i];
-            for (int l = 0; l < i; ++l)
-                sum = csub(sum, cmulc(J.XB[(int64_t)i * m + l], J.W2[(int64_t)c * ldy + l]));
-            const double2 d = J.diagZ[i];
-            J.W2[(int64_t)c * ldy + i] = cscale(cmul(d, sum), 1.0 / cabs2(d));  // sum / conj(d)
+    // C (m x n, ld m): minimum-norm solution of R_B (C P_B) = (Q_B^H D)(0:rB, :) with
+    // R_B = [R11 R12] (rB x m, upper trapezoidal, pivot order).  Complete
+    // orthogonal decomposition by reflectors from the right (the RZ reduction):
+    // for rows i = rB-1 .. 0 a reflector P_i on column i and columns rB..m-1
+    // zeroes row i of R12, so R_B P_{rB-1} ... P_0 = [T 0] with T upper
+    // triangular; then C P_B = P_{rB-1} ... P_0 [T^{-1} (Q_B^H D)(0:rB, :); 0].
+    // A reflector has 1 + m - rB entries (m - rB is small when B is close to
+    // full rank), so this costs O(rB^2 (m - rB)), not the O(m rB^2) of a QR of
+    // R_B^H.  V (1 + m - rB) x rB in XB holds the unit reflectors.
+    {
+        const int L = m - rB + 1;
+        double2* V = J.XB;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = nwarps();
+        // entry l of row r's reduced vector: column r (l = 0) or column rB + l - 1
+        auto col_of = [&](int r, int l) { return l == 0 ? r : rB + l - 1; };
+        if (L > 1) {
+            for (int i = rB - 1; i >= 0; --i) {
+                double sl = 0.0;
+                for (int l = threadIdx.x; l < L; l += blockDim.x)
+                    sl += cabs2(l == 0 ? J.diagB[i] : J.BD[(int64_t)col_of(i, l) * p + i]);
+                const double nx2 = block_sum(sl, red);
+                // a = conj(u) with u = row i's vector; P a = alpha e1, so u P = conj(alpha) e1
+                const double2 u0 = J.diagB[i];
+                const double2 a0 = make_double2(u0.x, -u0.y);
+                const double ax0 = sqrt(cabs2(a0));
+                const double2 ph = ax0 > 0.0 ? make_double2(a0.x / ax0, a0.y / ax0) : make_double2(1.0, 0.0);
+                const double nx = sqrt(nx2);
+                const double2 alpha = make_double2(-ph.x * nx, -ph.y * nx);
+                const double2 v0 = csub(a0, alpha);
+                const double nv2 = nx2 - ax0 * ax0 + cabs2(v0);
+                const double inv = nv2 > 0.0 ? 1.0 / sqrt(nv2) : 0.0;
+                for (int l = threadIdx.x; l < L; l += blockDim.x) {
+                    double2 v;
+                    if (l == 0) {
+                        v = cscale(v0, inv);
+                    } else {
+                        const double2 u = J.BD[(int64_t)col_of(i, l) * p + i];
+                        v = cscale(make_double2(u.x, -u.y), inv);
+                        J.BD[(int64_t)col_of(i, l) * p + i] = make_double2(0.0, 0.0);
+                    }
+                    V[(int64_t)i * L + l] = v;
+                }
+                __syncthreads();  // every thread has read R(i, i) before it is replaced
+                if (threadIdx.x == 0) J.diagB[i] = make_double2(alpha.x, -alpha.y);
+                // rows r < i: w <- w P_i = w - 2 (w . v) v^H
+                for (int r = w; r < i; r += nw) {
+                    double2 d = make_double2(0.0, 0.0);
+                    for (int l = lane; l < L; l += 32)
+                        d = cadd(d, cmul(J.BD[(int64_t)col_of(i, l) * p + r], V[(int64_t)i * L + l]));
+                    d = cscale(warp_sum2(d), 2.0);
+                    for (int l = lane; l < L; l += 32) {
+                        double2& x = J.BD[(int64_t)col_of(i, l) * p + r];
+                        x = csub(x, cmulc(V[(int64_t)i * L + l], d));  // d conj(v_l)
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // Y = T^{-1} (Q_B^H D)(0:rB, :) into W2 (rB x n, ld rB), T now in R_B's place
+        const int ldy = rB > 0 ? rB : 1;
+        cta_backsub(J.BD, p, J.diagB, rB, J.BD + (int64_t)m * p, p, n, J.W2, ldy);
+        for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+            const int i = (int)(e % m), c = (int)(e / m);
+            J.W3[e] = i < rB ? J.W2[(int64_t)c * ldy + i] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        // W3 <- P_{rB-1} ... P_0 W3 (P_0 first), P_i x = x - 2 v (v^H x)
+        if (L > 1) {
+            for (int i = 0; i < rB; ++i) {
+                for (int c = w; c < n; c += nw) {
+                    double2* x = J.W3 + (int64_t)c * m;
+                    double2 d = make_double2(0.0, 0.0);
+                    for (int l = lane; l < L; l += 32) d = cadd(d, cmulc(V[(int64_t)i * L + l], x[col_of(i, l)]));
+                    d = cscale(warp_sum2(d), 2.0);
+                    for (int l = lane; l < L; l += 32)
+                        x[col_of(i, l)] = csub(x[col_of(i, l)], cmul(V[(int64_t)i * L + l], d));
+                }
+                __syncthreads();
+            }
         }
     }
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
-        const int i = (int)(e % m), c = (int)(e / m);
-        J.W3[e] = i < rB ? J.W2[(int64_t)c * ldy + i] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    cta_apply_q(J.XB, m, m, rB, J.W3, m, n);
     for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
         const int i = (int)(e % m), c = (int)(e / m);
         J.C[(int64_t)c * m + J.permB[i]] = J.W3[e];

@@ -26,8 +26,7 @@ struct SBuildJob {
     double2* W1;    // kcap x max(m, n)
     double2* W2;    // min(p, m) x n
     double2* W3;    // m x n
-    double2* XB;    // m x min(p, m): R_B^H and its QR
-    double2* diagZ; // min(p, m)
+    double2* XB;    // m x min(p, m): reflectors of the RZ reduction of R_B, later G = Z* C F
     double2* XA;    // n x n: R_A^H, rotated by the Jacobi sweeps
     double* sig;    // n singular values of A
     int* keep;      // n: columns kept by the truncation
