@@ -468,7 +468,11 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                 if (!mbar_wait(smem_u32(&bar_full[stage]), fphase)) s_abort = 1;
                 const float4* src = reinterpret_cast<const float4*>(um_smem + stage * C::REC + 2 * C::TILE);
                 const int cnt = c == ce - 1 ? klast : UM_KC;  // staged sources of this chunk
-                const bool full_fast = wfast && cnt == UM_KC;
+                // the fast path also takes a body's ragged last chunk: its padding
+                // sources sit at delta = 0 (the source body's centre, away from
+                // every target of another body, so phi is finite) and have q = 0
+                // in B, so their products vanish
+                const bool full_fast = wfast;
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     // A columns of sources 8 half .. 8 half + 7:
