@@ -445,8 +445,8 @@ def test_near_field_reconstruction_3d(pkg):
     (kappa = 1, 16 x 32 collocation grid, MFS surface at half the radius, proxy
     at 1.6 radii), targets between each surface and its proxy sphere, GPU-built
     S against the oracle.  Relative 1e-15 perturbations of the oracle's point
-    sets move its own fields by up to 6.7e-10 (far) and 2.2e-10 (near): the
-    bounds are 1e-9 far (measured 4.8e-10) and 2e-9 near (measured 2.1e-10),
+    sets move its own fields by up to 6.7e-10 (far) and 2.4e-10 (near): the
+    bounds are 1e-9 far (measured 5.1e-10) and 2e-9 near (measured 2.3e-10),
     within 10x of that rounding sensitivity."""
     wl = geo.spheres()
     ref = orc.solve_workload(wl)
@@ -473,8 +473,8 @@ def test_gpu_built_ellipsoids_far_field_3d(pkg):
     grid, MFS surface at 0.7 scale, proxy at 1.5 times the largest semi-axis,
     ID to 1e-10 (k ~ 480 of m = 512).  FP64 and mixed-precision solves to a
     relative residual of 1e-11, scattered field at a far ring against the
-    oracle at 1e-9 (the oracle's own field moves by ~5e-11 under relative
-    1e-15 perturbations of its point sets)."""
+    oracle at 1e-9 (measured 1.2e-10; the oracle's own field moves by ~6e-11
+    under relative 1e-15 perturbations of its point sets)."""
     wl = geo.ellipsoids()
     ref = orc.solve_workload(wl)
     far = mi.far_targets(wl, 96, mode="ring")
@@ -496,11 +496,11 @@ def test_gpu_built_teardrops_with_corner_refinement(pkg):
     near field against the oracle.
 
     The corner-refined MFS matrix A has condition ~1e17; S (norm ~1.5e7) then
-    fixes the FP64 residual to ~u ||S|| (measured 8.7e-10 FP64, 1.2e-9 mixed),
+    fixes the FP64 residual to ~u ||S|| (measured 1.4e-9 FP64, 1.7e-9 mixed),
     the floor of any FP64 evaluation of this operator.  Relative 1e-15
     perturbations of the oracle's point sets move its own far field by 5.3e-10
     and its field on Gamma next to the corner by 3.8e-8: the bounds are 1e-9
-    far (measured 6.5e-10) and 1e-7 near (measured 2.3e-8)."""
+    far (measured 6.7e-10) and 1e-7 near (measured 1.8e-8)."""
     wl = geo.teardrops()
     ref = orc.solve_workload(wl)
     qm_ref = orc.reconstruct_mfs(wl, ref["sdata"], ref["layout"], ref["q"], ref["v"])
@@ -525,10 +525,10 @@ def test_gpu_built_cshapes_and_rods(pkg):
     semicircular caps) and two rods (rectangles with semicircular caps) on
     Gauss-Legendre panels refined 4 times at every joint, S built on the GPU,
     FP64 and mixed solves, far field and near field on Gamma against the
-    oracle.  ||S|| ~ 1.7e5 puts the FP64 residual floor near 1.6e-11.  The
+    oracle.  ||S|| ~ 1.7e5 puts the FP64 residual floor near 1.5e-11.  The
     oracle's own fields move by 5.6e-11 (far) and 1.8e-9 (on Gamma next to the
     joints) under relative 1e-15 perturbations of its point sets: the bounds
-    are 5e-10 far (measured 2.4e-10) and 1.5e-8 near (measured 7.5e-9)."""
+    are 5e-10 far (measured 2.3e-10) and 1.5e-8 near (measured 7.9e-9)."""
     wl = geo.cshapes_rods()
     ref = orc.solve_workload(wl)
     qm_ref = orc.reconstruct_mfs(wl, ref["sdata"], ref["layout"], ref["q"], ref["v"])
