@@ -35,6 +35,22 @@ __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) {
     return make_double2(a.x * s, a.y * s);
 }
 __host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// Complex multiply-adds as four fused multiply-adds each (the FP64 pipe issues
+// one per slot; a product then a sum would take six):
+// acc + a b, acc + conj(a) b, acc - a b, acc - conj(a) b, and s + |a|^2.
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double2 cfmsc(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double abs2_acc(double2 a, double s) { return fma(a.x, a.x, fma(a.y, a.y, s)); }
 __host__ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

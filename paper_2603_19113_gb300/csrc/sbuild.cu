@@ -181,14 +181,14 @@ __device__ void householder_step(double2* A, int ld, int rows, int j, int ncols,
     for (int c = j + 1 + w; c < ntot; c += nwarps()) {
         double2* cc = A + (int64_t)c * ld;
         double2 d = make_double2(0.0, 0.0);
-        for (int i = j + lane; i < rows; i += 32) d = cadd(d, cmulc(s_v[i - j], cc[i]));
+        for (int i = j + lane; i < rows; i += 32) d = cfmac(s_v[i - j], cc[i], d);
         d = warp_sum2(d);
         d = cscale(d, 2.0);
         double s = 0.0;
         for (int i = j + lane; i < rows; i += 32) {
-            const double2 nv = csub(cc[i], cmul(s_v[i - j], d));
+            const double2 nv = cfms(s_v[i - j], d, cc[i]);
             cc[i] = nv;
-            if (i > j) s += cabs2(nv);
+            if (i > j) s = abs2_acc(nv, s);
         }
         if (nrm2 && c < ncols) {
             s = warp_sum(s);
@@ -236,9 +236,9 @@ __device__ int cta_jacobi(double2* X, int ldx, int rows, int r, double2* Jm, int
                 double2 c = make_double2(0.0, 0.0);
                 for (int l = lane; l < rows; l += 32) {
                     const double2 u = xi[l], v = xj[l];
-                    a += cabs2(u);
-                    b += cabs2(v);
-                    c = cadd(c, cmulc(u, v));
+                    a = abs2_acc(u, a);
+                    b = abs2_acc(v, b);
+                    c = cfmac(u, v, c);
                 }
                 a = warp_sum(a);
                 b = warp_sum(b);
@@ -368,7 +368,7 @@ __device__ void cta_backsub(const double2* Rm, int ldr, const double2* diag, int
         for (int i = n - 1; i >= 0; --i) {
             double2 s = Bm[(int64_t)c * ldb + i];
             for (int l = i + 1; l < n; ++l)
-                s = csub(s, cmul(Rm[(int64_t)l * ldr + i], X[(int64_t)c * ldx + l]));
+                s = cfms(Rm[(int64_t)l * ldr + i], X[(int64_t)c * ldx + l], s);
             const double2 d = diag[i];
             const double id = 1.0 / cabs2(d);
             X[(int64_t)c * ldx + i] = cscale(cmulc(d, s), id);  // s / d
@@ -424,7 +424,7 @@ __device__ __forceinline__ void sbuild_phase1(SBuildJob& J, double kappa, double
         for (int64_t e = threadIdx.x; e < (int64_t)d * m; e += blockDim.x) {
             const int i = (int)(e % d), j = (int)(e / d);
             double2 sum = make_double2(0.0, 0.0);
-            for (int l = 0; l < p; ++l) sum = cadd(sum, cmul(J.OM[(int64_t)l * d + i], J.BD[(int64_t)j * p + l]));
+            for (int l = 0; l < p; ++l) sum = cfma(J.OM[(int64_t)l * d + i], J.BD[(int64_t)j * p + l], sum);
             J.Y[e] = sum;
         }
         __syncthreads();
@@ -515,11 +515,11 @@ __device__ __forceinline__ void sbuild_phase2(SBuildJob& J, double rcond, Red& r
                 for (int r = w; r < i; r += nw) {
                     double2 d = make_double2(0.0, 0.0);
                     for (int l = lane; l < L; l += 32)
-                        d = cadd(d, cmul(J.BD[(int64_t)col_of(i, l) * p + r], V[(int64_t)i * L + l]));
+                        d = cfma(J.BD[(int64_t)col_of(i, l) * p + r], V[(int64_t)i * L + l], d);
                     d = cscale(warp_sum2(d), 2.0);
                     for (int l = lane; l < L; l += 32) {
                         double2& x = J.BD[(int64_t)col_of(i, l) * p + r];
-                        x = csub(x, cmulc(V[(int64_t)i * L + l], d));  // d conj(v_l)
+                        x = cfmsc(V[(int64_t)i * L + l], d, x);  // x - conj(v_l) d
                     }
                 }
                 __syncthreads();
@@ -539,10 +539,10 @@ __device__ __forceinline__ void sbuild_phase2(SBuildJob& J, double rcond, Red& r
                 for (int c = w; c < n; c += nw) {
                     double2* x = J.W3 + (int64_t)c * m;
                     double2 d = make_double2(0.0, 0.0);
-                    for (int l = lane; l < L; l += 32) d = cadd(d, cmulc(V[(int64_t)i * L + l], x[col_of(i, l)]));
+                    for (int l = lane; l < L; l += 32) d = cfmac(V[(int64_t)i * L + l], x[col_of(i, l)], d);
                     d = cscale(warp_sum2(d), 2.0);
                     for (int l = lane; l < L; l += 32)
-                        x[col_of(i, l)] = csub(x[col_of(i, l)], cmul(V[(int64_t)i * L + l], d));
+                        x[col_of(i, l)] = cfms(V[(int64_t)i * L + l], d, x[col_of(i, l)]);
                 }
                 __syncthreads();
             }
@@ -595,7 +595,7 @@ __device__ __forceinline__ void sbuild_phase3(SBuildJob& J, double rcond, Red& r
     // singular values = column norms of X J
     for (int i = w; i < rA; i += nwarps()) {
         double sum = 0.0;
-        for (int l = lane; l < n; l += 32) sum += cabs2(J.XA[(int64_t)i * n + l]);
+        for (int l = lane; l < n; l += 32) sum = abs2_acc(J.XA[(int64_t)i * n + l], sum);
         sum = warp_sum(sum);
         if (lane == 0) J.sig[i] = sqrt(sum);
     }
@@ -634,7 +634,7 @@ __device__ __forceinline__ void sbuild_phase3(SBuildJob& J, double rcond, Red& r
     for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
         const int i = (int)(e % k), c = (int)(e / k);
         double2 sum = make_double2(0.0, 0.0);
-        for (int l = 0; l < m; ++l) sum = cadd(sum, cmul(J.Zs[(int64_t)l * k + i], J.C[(int64_t)c * m + l]));
+        for (int l = 0; l < m; ++l) sum = cfma(J.Zs[(int64_t)l * k + i], J.C[(int64_t)c * m + l], sum);
         J.W1[e] = sum;
     }
     // H = J_r^H (Q_A^H U)(0:rA, :)  (r x k, ld r) into W3
@@ -643,7 +643,7 @@ __device__ __forceinline__ void sbuild_phase3(SBuildJob& J, double rcond, Red& r
         const int i = (int)(e % ldh), c = (int)(e / ldh);
         double2 sum = make_double2(0.0, 0.0);
         for (int l = 0; l < rA; ++l)
-            sum = cadd(sum, cmulc(J.JA[(int64_t)i * n + l], J.AU[(int64_t)(n + c) * m + l]));
+            sum = cfmac(J.JA[(int64_t)i * n + l], J.AU[(int64_t)(n + c) * m + l], sum);
         J.W3[e] = sum;
     }
     __syncthreads();
@@ -651,7 +651,7 @@ __device__ __forceinline__ void sbuild_phase3(SBuildJob& J, double rcond, Red& r
     for (int64_t e = threadIdx.x; e < (int64_t)k * r; e += blockDim.x) {
         const int i = (int)(e % k), c = (int)(e / k);
         double2 sum = make_double2(0.0, 0.0);
-        for (int l = 0; l < n; ++l) sum = cadd(sum, cmul(J.W1[(int64_t)l * k + i], J.FA[(int64_t)c * n + l]));
+        for (int l = 0; l < n; ++l) sum = cfma(J.W1[(int64_t)l * k + i], J.FA[(int64_t)c * n + l], sum);
         J.XB[e] = sum;
     }
     __syncthreads();
@@ -660,7 +660,7 @@ __device__ __forceinline__ void sbuild_phase3(SBuildJob& J, double rcond, Red& r
     for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
         const int i = (int)(e % k), c = (int)(e / k);
         double2 sum = make_double2(0.0, 0.0);
-        for (int l = 0; l < r; ++l) sum = cadd(sum, cmul(J.XB[(int64_t)l * k + i], J.W3[(int64_t)c * ldh + l]));
+        for (int l = 0; l < r; ++l) sum = cfma(J.XB[(int64_t)l * k + i], J.W3[(int64_t)c * ldh + l], sum);
         J.S[e] = sum;
         sq += cabs2(sum);
     }
