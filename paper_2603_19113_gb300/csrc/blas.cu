@@ -3,6 +3,12 @@
 // z_tau = x_tau + S_tau y_tau for every body tau (the "I +" and "S" of
 // eq. mbody2, Sec. 2.2), with S_tau k_tau x k_tau column-major and shared
 // between bodies of one shape.  Vectors are stored [nrhs][N].
+#include <cuda.h>
+
+#include <atomic>
+#include <string>
+
+#include "bulk.cuh"
 #include "common.cuh"
 
 namespace {
@@ -566,15 +572,9 @@ __global__ void __launch_bounds__(256) ts_trsm_kernel(V* __restrict__ B, const i
     }
 }
 
-// FP32 tall-skinny products for block widths kb <= 8 and even N: 16-byte
-// loads (two consecutive rows of one column), the new block staged once per
-// CTA in shared memory, and no cross-warp reduction in the Gram product.
-constexpr int TG_W = 8;       // warps per CTA
-constexpr int TG_A = 4;       // basis columns per warp
-constexpr int TG_ROWS = 256;  // rows per shared-memory stage of B
-constexpr int TU_ROWS = 64;   // rows per CTA of the update (two per lane)
-
-__device__ __forceinline__ float4 ldg4(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+// FP32 tall-skinny products for block widths kb <= 8 and even N: the basis
+// streamed through shared memory by bulk copies, 16-byte operands (two
+// consecutive rows of one column), no cross-warp reduction in the Gram product.
 
 // One step of a warp reduce-scatter: 2*HALF values per lane become HALF,
 // lanes with bit MASK set keep the upper half.  The additions happen in an
@@ -590,72 +590,157 @@ __device__ __forceinline__ void fold_half(float (&v)[64], int lane) {
     }
 }
 
-// partial[(b * ka + a) * nblk + blk] = sum over rows [blk*chunk, (blk+1)*chunk)
-// of conj(A_a) B_b.  Warp w of CTA (blk, y) owns columns a0 .. a0+3,
-// a0 = (8 y + w) * 4; per lane the sums run over its rows in order, then a
-// reduce-scatter leaves pair (a0 + lane / 8, lane % 8) on each lane.
-__global__ void __launch_bounds__(256, 2) ts_gram32_kernel(const float2* __restrict__ A, const int ka,
-                                                           const float2* __restrict__ B, const int kb,
-                                                           const int64_t N, const int64_t chunk,
-                                                           double2* __restrict__ partial,
-                                                           const int nblk) {
-    __shared__ float4 s_b[8][TG_ROWS / 2];
+// FP32 block Gram product V^H W, the basis streamed through a ring of
+// shared-memory stages by 2D tensor copies (TMA).
+//
+// CTA (blk, y): basis columns 32 y .. 32 y + 31 over rows [blk chunk,
+// (blk + 1) chunk).  The copy warp (warp 8, one lane) fills stage t with two
+// boxes: rows n0 + 64 t .. n0 + 64 t + 63 of those columns (a bca x 512-byte
+// box of the basis's tensor map, bca = min(32, ka)) and of the kb <= 8
+// columns of W (kb x 512
+// bytes), column c of the stage at byte 512 c, W's columns after the 32 basis
+// columns; both complete on full[t % S].  Rows past N and columns past ka
+// arrive as zeros.  Compute warp w owns basis columns 4 w .. 4 w + 3; lane l
+// takes row pair l of each stage (one 16-byte load per column), accumulates
+// its 4 x 8 complex sums in order over the stages, and releases the stage on
+// empty[t % S].  A reduce-scatter across the warp then leaves one (column,
+// RHS) pair per lane.  Waits are bounded: on a timeout the CTA sets *err,
+// writes NaN partials and waits (bounded) for its copies in flight.
+constexpr int RG_COLS = 32;
+constexpr int RG_ROWS = 64;
+constexpr int RG_STAGES = 4;
+constexpr int RG_THREADS = 288;
+constexpr int RG_COLBYTES = RG_ROWS * 8;
+constexpr int RG_STAGE = (RG_COLS + 8) * RG_COLBYTES;
+constexpr int RG_SMEM = RG_STAGES * RG_STAGE;
+constexpr unsigned long long RING_WAIT_NS = 2000000000ull;
+
+__global__ void __launch_bounds__(RG_THREADS, 2) ts_gram32_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                  const int ka, const int bca,
+                                                                  const __grid_constant__ CUtensorMap tmB,
+                                                                  const int kb, const int64_t N,
+                                                                  const int64_t chunk,
+                                                                  double2* __restrict__ partial,
+                                                                  const int nblk, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char rg_smem[];
+    __shared__ __align__(8) uint64_t full[RG_STAGES];
+    __shared__ __align__(8) uint64_t empty[RG_STAGES];
+    __shared__ volatile int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int blk = blockIdx.x;
-    const int a0 = (blockIdx.y * TG_W + warp) * TG_A;
-    const bool active = a0 < ka;
+    const int col0 = blockIdx.y * RG_COLS;
+    const int ncol = min(RG_COLS, ka - col0);
+    const int nact = (ncol + 3) >> 2;  // compute warps that own columns
     const int64_t n0 = (int64_t)blk * chunk, n1 = min(N, n0 + chunk);
+    const int nst = n1 > n0 ? (int)((n1 - n0 + RG_ROWS - 1) / RG_ROWS) : 0;
+    const uint32_t sbase = smem_u32(rg_smem);
+    if (sbase & 127u) {  // tensor copies need 128-byte aligned stages: report, copy nothing
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RG_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), (uint32_t)nact);
+        }
+        mbar_init_fence();
+        s_abort = 0;
+    }
+    // columns no copy writes (basis columns bca .. 31 when ka < 32, W columns
+    // kb .. 7) are zero in every stage, so the products need no guards; the
+    // copies zero-fill rows past N and columns past ka themselves
+    {
+        constexpr int W4 = RG_COLBYTES / 16;  // float4 per column
+        for (int s = 0; s < RG_STAGES; ++s) {
+            float4* st4 = reinterpret_cast<float4*>(rg_smem + s * RG_STAGE);
+            for (int i = threadIdx.x; i < (RG_COLS - bca) * W4; i += blockDim.x)
+                st4[bca * W4 + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = threadIdx.x; i < (8 - kb) * W4; i += blockDim.x)
+                st4[(RG_COLS + kb) * W4 + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    if (warp == RG_THREADS / 32 - 1) {
+        // ---------------- copy warp ----------------
+        int t = 0;
+        for (; t < nst; ++t) {
+            const int s = t % RG_STAGES;
+            if (t >= RG_STAGES) {
+                int ok = 1;
+                if (lane == 0)
+                    ok = mbar_wait(smem_u32(&empty[s]), (uint32_t)((t / RG_STAGES - 1) & 1), RING_WAIT_NS) &&
+                         !s_abort;
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    if (lane == 0) s_abort = 1;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                const int x = 2 * (int)(n0 + (int64_t)t * RG_ROWS);  // FP32 elements: a multiple of 128
+                const uint32_t fb = smem_u32(&full[s]);
+                const uint32_t st = sbase + (uint32_t)(s * RG_STAGE);
+                mbar_arrive_expect(fb, (uint32_t)(bca + kb) * RG_COLBYTES);
+                tensor_copy_2d(st, &tmA, x, col0, fb);
+                tensor_copy_2d(st + RG_COLS * RG_COLBYTES, &tmB, x, 0, fb);
+            }
+            __syncwarp();
+        }
+        // every issued copy has landed before the CTA (and its shared memory) ends
+        if (lane == 0)
+            for (int u = max(0, t - RG_STAGES); u < t; ++u)
+                mbar_wait(smem_u32(&full[u % RG_STAGES]), (uint32_t)((u / RG_STAGES) & 1), RING_WAIT_NS);
+        return;
+    }
+    if (warp >= nact) return;
+    // ---------------- compute warps ----------------
+    const int a0 = 4 * warp;
     float v[64];
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] = 0.f;
-    for (int64_t s0 = n0; s0 < n1; s0 += TG_ROWS) {
-        const int pairs = (int)(min((int64_t)TG_ROWS, n1 - s0) >> 1);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < 8 * (TG_ROWS / 2); idx += blockDim.x) {
-            const int b = idx / (TG_ROWS / 2), p = idx - b * (TG_ROWS / 2);
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (b < kb && p < pairs) x = ldg4(B + (int64_t)b * N + s0 + 2 * p);
-            s_b[b][p] = x;
+    bool ok = true;
+    for (int t = 0; t < nst; ++t) {
+        const int s = t % RG_STAGES;
+        if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((t / RG_STAGES) & 1), RING_WAIT_NS) || s_abort) {
+            ok = false;
+            break;
         }
-        __syncthreads();
-        if (!active) continue;
-#pragma unroll 2
-        for (int pp = 0; pp < TG_ROWS / 64; ++pp) {
-            const int p = lane + 32 * pp;
-            if (p < pairs) {
-                float4 av[TG_A];
+        const unsigned char* st = rg_smem + s * RG_STAGE + lane * 16;
+        float4 av[4];
 #pragma unroll
-                for (int a = 0; a < TG_A; ++a)
-                    av[a] = (a0 + a < ka) ? ldg4(A + (int64_t)(a0 + a) * N + s0 + 2 * p)
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(st + (a0 + a) * RG_COLBYTES);
 #pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const float4 bv = s_b[b][p];
+        for (int b = 0; b < 8; ++b) {
+            const float4 bv = *reinterpret_cast<const float4*>(st + (RG_COLS + b) * RG_COLBYTES);
 #pragma unroll
-                    for (int a = 0; a < TG_A; ++a) {
-                        float& re = v[(a * 8 + b) * 2];
-                        float& im = v[(a * 8 + b) * 2 + 1];
-                        re = fmaf(av[a].x, bv.x, re);
-                        re = fmaf(av[a].y, bv.y, re);
-                        re = fmaf(av[a].z, bv.z, re);
-                        re = fmaf(av[a].w, bv.w, re);
-                        im = fmaf(av[a].x, bv.y, im);
-                        im = fmaf(-av[a].y, bv.x, im);
-                        im = fmaf(av[a].z, bv.w, im);
-                        im = fmaf(-av[a].w, bv.z, im);
-                    }
-                }
+            for (int a = 0; a < 4; ++a) {
+                float& re = v[(a * 8 + b) * 2];
+                float& im = v[(a * 8 + b) * 2 + 1];
+                re = fmaf(av[a].x, bv.x, re);
+                re = fmaf(av[a].y, bv.y, re);
+                re = fmaf(av[a].z, bv.z, re);
+                re = fmaf(av[a].w, bv.w, re);
+                im = fmaf(av[a].x, bv.y, im);
+                im = fmaf(-av[a].y, bv.x, im);
+                im = fmaf(av[a].z, bv.w, im);
+                im = fmaf(-av[a].w, bv.z, im);
             }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
-    if (!active) return;
+    if (!ok) {
+        s_abort = 1;
+        if (lane == 0) atomicExch(err, 1);
+    }
     fold_half<32, 16>(v, lane);
     fold_half<16, 8>(v, lane);
     fold_half<8, 4>(v, lane);
     fold_half<4, 2>(v, lane);
     fold_half<2, 1>(v, lane);
-    const int a = a0 + (lane >> 3), b = lane & 7;
-    if (a < ka && b < kb) partial[((int64_t)b * ka + a) * nblk + blk] = make_double2(v[0], v[1]);
+    const int a = col0 + a0 + (lane >> 3), b = lane & 7;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    if (a < ka && b < kb)
+        partial[((int64_t)b * ka + a) * nblk + blk] = ok ? make_double2(v[0], v[1]) : make_double2(nanv, nanv);
 }
 
 // coef[a * 8 + b] = alpha H(a, b) in FP32 (H ka x kb column-major), zero for b >= kb
@@ -672,64 +757,169 @@ __global__ void ts_coef32_kernel(const double2* __restrict__ H, const int ka, co
     coef[i] = c;
 }
 
-// B_b += sum_a A_a coef(a, b) on rows [64 blockIdx.x, +64): lane = two rows,
-// warp w sums its share of the columns in order, the eight warp sums are
-// added in warp order.
-__global__ void __launch_bounds__(256) ts_update32_kernel(const float2* __restrict__ A, const int ka,
-                                                          const float2* __restrict__ coef,
-                                                          float2* __restrict__ B, const int kb,
-                                                          const int64_t N) {
-    __shared__ float4 s_red[TG_W][8][32];
+// B_b += sum_a A_a coef(a, b) (kb <= 8), the basis streamed through a ring of
+// shared-memory stages by 2D tensor copies (TMA).
+//
+// CTA x: rows [64 x, 64 x + 64), two per lane.  The copy warp (warp 4, one
+// lane) fills stage t with those rows of basis columns 16 t .. 16 t + 15 (a
+// bca x 512-byte box of the basis's tensor map, bca = min(16, ka); rows past N and columns past
+// ka arrive as zeros) and with their FP32 coefficients (16 x 8 float2, one
+// contiguous bulk copy of up to 1 KB), both completing on full[t % S].
+// Compute warp w takes columns 16 t + 4 w .. 16 t + 4 w + 3 of every stage,
+// so its sums run over columns in order; after the last stage the four warp
+// sums are added in warp order through shared memory (the ring, by then
+// idle) and the read-modify-write of B follows.  Waits are bounded as in the
+// Gram kernel.
+constexpr int RU_ROWS = 64;
+constexpr int RU_COLS = 16;
+constexpr int RU_WARPS = 4;
+constexpr int RU_STAGES = 3;
+constexpr int RU_THREADS = (RU_WARPS + 1) * 32;
+constexpr int RU_COLBYTES = RU_ROWS * 8;
+constexpr int RU_STAGE = RU_COLS * RU_COLBYTES + RU_COLS * 8 * 8;
+constexpr int RU_SMEM = RU_STAGES * RU_STAGE;
+static_assert(RU_SMEM >= RU_WARPS * 8 * 32 * 16, "the ring holds the cross-warp reduction");
+
+__global__ void __launch_bounds__(RU_THREADS, 7) ts_update32_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                   const int ka, const int bca,
+                                                                   const float2* __restrict__ coef,
+                                                                   float2* __restrict__ B, const int kb,
+                                                                   const int64_t N, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char ru_smem[];
+    __shared__ __align__(8) uint64_t full[RU_STAGES];
+    __shared__ __align__(8) uint64_t empty[RU_STAGES];
+    __shared__ volatile int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * TU_ROWS + 2 * lane;
-    const int per = (ka + TG_W - 1) / TG_W;
-    const int c0 = min(ka, warp * per), c1 = min(ka, c0 + per);
+    const int64_t r0 = (int64_t)blockIdx.x * RU_ROWS;
+    const int rows = (int)min((int64_t)RU_ROWS, N - r0);
+    const int nst = (ka + RU_COLS - 1) / RU_COLS;
+    const uint32_t sbase = smem_u32(ru_smem);
+    if (sbase & 127u) {  // tensor copies need 128-byte aligned stages: report, copy nothing
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RU_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), RU_WARPS);
+        }
+        mbar_init_fence();
+        s_abort = 0;
+    }
+    // the whole ring starts at zero, so a stage's columns past ka (zero basis
+    // columns from the copy, or never copied when ka < 16) meet finite
+    // coefficients and the products need no guards; the proxy fence orders
+    // these stores before the copies that later overwrite them
+    for (int i = threadIdx.x; i < RU_SMEM / 16; i += blockDim.x)
+        reinterpret_cast<float4*>(ru_smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (warp == RU_WARPS) {
+        // ---------------- copy warp ----------------
+        int t = 0;
+        for (; t < nst; ++t) {
+            const int s = t % RU_STAGES;
+            if (t >= RU_STAGES) {
+                int ok = 1;
+                if (lane == 0)
+                    ok = mbar_wait(smem_u32(&empty[s]), (uint32_t)((t / RU_STAGES - 1) & 1), RING_WAIT_NS) &&
+                         !s_abort;
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    if (lane == 0) s_abort = 1;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                const int c0 = t * RU_COLS, cols = min(RU_COLS, ka - c0);
+                const uint32_t fb = smem_u32(&full[s]);
+                const uint32_t st = sbase + (uint32_t)(s * RU_STAGE);
+                mbar_arrive_expect(fb, (uint32_t)(bca * RU_COLBYTES + cols * 64));
+                tensor_copy_2d(st, &tmA, (int)(2 * r0), c0, fb);  // x: a multiple of 128 FP32 elements
+                bulk_copy(st + RU_COLS * RU_COLBYTES, coef + (int64_t)c0 * 8, (uint32_t)cols * 64u, fb);
+            }
+            __syncwarp();
+        }
+        if (lane == 0)
+            for (int u = max(0, t - RU_STAGES); u < t; ++u)
+                mbar_wait(smem_u32(&full[u % RU_STAGES]), (uint32_t)((u / RU_STAGES) & 1), RING_WAIT_NS);
+        return;
+    }
+    // ---------------- compute warps ----------------
     float acc[8][4];
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.f;
-    if (r0 < N) {
-        const float4* __restrict__ c4 = reinterpret_cast<const float4*>(coef);
-#pragma unroll 4
-        for (int a = c0; a < c1; ++a) {
-            const float4 av = ldg4(A + (int64_t)a * N + r0);
+    bool ok = true;
+    const bool live = 2 * lane < rows;
+    for (int t = 0; t < nst; ++t) {
+        const int s = t % RU_STAGES;
+        if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((t / RU_STAGES) & 1), RING_WAIT_NS) || s_abort) {
+            ok = false;
+            break;
+        }
+        const unsigned char* st = ru_smem + s * RU_STAGE;
+        const float4* c4 = reinterpret_cast<const float4*>(st + RU_COLS * RU_COLBYTES);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 h = __ldg(c4 + (int64_t)a * 4 + q);
-                float* x = acc[2 * q];
-                float* y = acc[2 * q + 1];
-                x[0] = fmaf(av.x, h.x, fmaf(-av.y, h.y, x[0]));
-                x[1] = fmaf(av.x, h.y, fmaf(av.y, h.x, x[1]));
-                x[2] = fmaf(av.z, h.x, fmaf(-av.w, h.y, x[2]));
-                x[3] = fmaf(av.z, h.y, fmaf(av.w, h.x, x[3]));
-                y[0] = fmaf(av.x, h.z, fmaf(-av.y, h.w, y[0]));
-                y[1] = fmaf(av.x, h.w, fmaf(av.y, h.z, y[1]));
-                y[2] = fmaf(av.z, h.z, fmaf(-av.w, h.w, y[2]));
-                y[3] = fmaf(av.z, h.w, fmaf(av.w, h.z, y[3]));
+        for (int k = 0; k < RU_COLS / RU_WARPS; ++k) {
+            const int c = RU_COLS / RU_WARPS * warp + k;
+            {
+                const float4 av = *reinterpret_cast<const float4*>(st + c * RU_COLBYTES + lane * 16);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 h = c4[c * 4 + q];
+                    float* x = acc[2 * q];
+                    float* y = acc[2 * q + 1];
+                    x[0] = fmaf(av.x, h.x, fmaf(-av.y, h.y, x[0]));
+                    x[1] = fmaf(av.x, h.y, fmaf(av.y, h.x, x[1]));
+                    x[2] = fmaf(av.z, h.x, fmaf(-av.w, h.y, x[2]));
+                    x[3] = fmaf(av.z, h.y, fmaf(av.w, h.x, x[3]));
+                    y[0] = fmaf(av.x, h.z, fmaf(-av.y, h.w, y[0]));
+                    y[1] = fmaf(av.x, h.w, fmaf(av.y, h.z, y[1]));
+                    y[2] = fmaf(av.z, h.z, fmaf(-av.w, h.w, y[2]));
+                    y[3] = fmaf(av.z, h.w, fmaf(av.w, h.z, y[3]));
+                }
             }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
     }
+    if (!ok) {
+        s_abort = 1;
+        if (lane == 0) atomicExch(err, 1);
+    }
+    // cross-warp sums through the ring: every stage has been consumed by every
+    // compute warp once all of them pass this barrier (the copy warp is not in it)
+    asm volatile("bar.sync 1, %0;" ::"n"(RU_WARPS * 32) : "memory");
+    float4* red = reinterpret_cast<float4*>(ru_smem);  // [warp][b][lane]
 #pragma unroll
-    for (int b = 0; b < 8; ++b) s_red[warp][b][lane] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
-    __syncthreads();
-    const int b = threadIdx.x >> 5;
-    const int64_t row = (int64_t)blockIdx.x * TU_ROWS + 2 * lane;
-    if (b < kb && row < N) {
-        float4 t = s_red[0][b][lane];
+    for (int b = 0; b < 8; ++b) red[(warp * 8 + b) * 32 + lane] = make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+    asm volatile("bar.sync 1, %0;" ::"n"(RU_WARPS * 32) : "memory");
+    const bool abort = s_abort != 0;
 #pragma unroll
-        for (int w = 1; w < TG_W; ++w) {
-            const float4 u = s_red[w][b][lane];
-            t.x += u.x;
-            t.y += u.y;
-            t.z += u.z;
-            t.w += u.w;
+    for (int k = 0; k < 8 / RU_WARPS; ++k) {
+        const int b = warp * (8 / RU_WARPS) + k;
+        if (b < kb && live) {
+            float4 tsum = red[b * 32 + lane];
+#pragma unroll
+            for (int w = 1; w < RU_WARPS; ++w) {
+                const float4 u = red[(w * 8 + b) * 32 + lane];
+                tsum.x += u.x;
+                tsum.y += u.y;
+                tsum.z += u.z;
+                tsum.w += u.w;
+            }
+            float4* o = reinterpret_cast<float4*>(B + (int64_t)b * N + r0 + 2 * lane);
+            float4 x = *o;
+            if (abort) {
+                const float nanv = __int_as_float(0x7fc00000);
+                x = make_float4(nanv, nanv, nanv, nanv);
+            } else {
+                x.x += tsum.x;
+                x.y += tsum.y;
+                x.z += tsum.z;
+                x.w += tsum.w;
+            }
+            *o = x;
         }
-        float4* o = reinterpret_cast<float4*>(B + (int64_t)b * N + row);
-        float4 x = *o;
-        x.x += t.x;
-        x.y += t.y;
-        x.z += t.z;
-        x.w += t.w;
-        *o = x;
     }
 }
 
@@ -872,13 +1062,63 @@ namespace {
 // the FP32 kernels need kb <= 8 and even N (16-byte loads of row pairs)
 bool ts_fast(bool f32, int kb, int64_t N) { return f32 && kb <= 8 && (N % 2) == 0; }
 
-// rows per Gram block of the FP32 kernel: a multiple of the stage, about
-// four CTAs per resident slot over the whole grid
+// rows per Gram block of the FP32 kernel: a multiple of the stage, the grid at
+// most two full waves of the two CTAs per SM that the ring's shared memory
+// allows (a few CTAs of a third wave would cost a whole wave's time)
 int64_t ts_gram32_chunk(int64_t N, int ka) {
-    const int64_t tiles = (ka + TG_W * TG_A - 1) / (TG_W * TG_A);
-    const int64_t want = std::max<int64_t>(1, (8LL * mbs_num_sms() + tiles - 1) / tiles);
+    const int64_t tiles = (ka + RG_COLS - 1) / RG_COLS;
+    const int64_t want = std::max<int64_t>(1, 4LL * mbs_num_sms() / tiles);  // CTAs <= 2 waves
     const int64_t rows = (N + want - 1) / want;
-    return std::max<int64_t>(TG_ROWS, (rows + TG_ROWS - 1) / TG_ROWS * TG_ROWS);
+    return std::max<int64_t>(RG_ROWS, (rows + RG_ROWS - 1) / RG_ROWS * RG_ROWS);
+}
+
+// dynamic shared memory above 48 KB, set once per device and kernel (keeps the
+// call out of captured CUDA graphs)
+template <typename F>
+void ring_smem_attr(F* kernel, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    MBS_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return;
+    MBS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.fetch_or(bit);
+}
+std::atomic<unsigned long long> g_gram_attr{0}, g_update_attr{0};
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    if (!fn) throw MbsError{MBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+    return fn;
+}
+
+// Tensor map over cols columns of N complex FP32 values at base (column c at
+// base + c N): FP32 elements, dimensions {2 N, cols}, row stride 8 N bytes,
+// box {128 elements (64 complex rows), boxcols columns}; outside it, zeros.
+CUtensorMap column_map(const void* base, int64_t N, int cols, int boxcols) {
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)(N * 8)};
+    const cuuint32_t box[2] = {2 * RG_ROWS, (cuuint32_t)boxcols};
+    const cuuint32_t step[2] = {1, 1};
+    const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+                                      box, step, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        throw MbsError{MBS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+    return m;
 }
 
 void check_aligned16(const void* p, const char* what) {
@@ -899,7 +1139,7 @@ int ts_gram_blocks(int64_t N, int ka, int kb, bool f32) {
 
 template <typename V>
 void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* C,
-                    double2* scratch, int nblk, cudaStream_t st) {
+                    double2* scratch, int nblk, cudaStream_t st, int* err) {
     if (ka == 0 || kb == 0) return;
     if (N == 0) {
         MBS_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)ka * kb * sizeof(double2), st));
@@ -911,10 +1151,12 @@ void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* 
             throw MbsError{MBS_ERR_ARG, "launch_ts_gram: block count does not match ts_gram_blocks"};
         check_aligned16(A, "launch_ts_gram");
         check_aligned16(B, "launch_ts_gram");
-        dim3 g((unsigned)nblk, (unsigned)((ka + TG_W * TG_A - 1) / (TG_W * TG_A)));
-        ts_gram32_kernel<<<g, 256, 0, st>>>(reinterpret_cast<const float2*>(A), ka,
-                                            reinterpret_cast<const float2*>(B), kb, N, chunk, scratch,
-                                            nblk);
+        if (!err) throw MbsError{MBS_ERR_ARG, "launch_ts_gram: no device error flag"};
+        ring_smem_attr(ts_gram32_kernel, RG_SMEM, g_gram_attr);
+        const int bca = std::min(RG_COLS, ka);
+        const CUtensorMap tmA = column_map(A, N, ka, bca), tmB = column_map(B, N, kb, kb);
+        dim3 g((unsigned)nblk, (unsigned)((ka + RG_COLS - 1) / RG_COLS));
+        ts_gram32_kernel<<<g, RG_THREADS, RG_SMEM, st>>>(tmA, ka, bca, tmB, kb, N, chunk, scratch, nblk, err);
     } else {
         dim3 g((unsigned)nblk, (unsigned)((ka + TSG_A - 1) / TSG_A), (unsigned)((kb + TSG_B - 1) / TSG_B));
         ts_gram_kernel<V><<<g, 256, 0, st>>>(A, ka, B, kb, N, scratch, nblk);
@@ -926,17 +1168,20 @@ void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* 
 
 template <typename V>
 void launch_ts_update(const V* A, int ka, const double2* H, double alpha, V* B, int kb, int64_t N,
-                      cudaStream_t st, float2* coef) {
+                      cudaStream_t st, float2* coef, int* err) {
     if (ka == 0 || kb == 0 || N == 0) return;
     if (kb > 16) throw MbsError{MBS_ERR_ARG, "launch_ts_update: more than 16 columns"};
-    if (coef && ts_fast(sizeof(V) == 8, kb, N)) {
+    if (coef && err && ts_fast(sizeof(V) == 8, kb, N)) {
         check_aligned16(A, "launch_ts_update");
         check_aligned16(B, "launch_ts_update");
         check_aligned16(coef, "launch_ts_update");
         ts_coef32_kernel<<<nblocks((int64_t)ka * 8, 256), 256, 0, st>>>(H, ka, kb, alpha, coef);
         MBS_CHECK_LAUNCH();
-        ts_update32_kernel<<<(unsigned)((N + TU_ROWS - 1) / TU_ROWS), 256, 0, st>>>(
-            reinterpret_cast<const float2*>(A), ka, coef, reinterpret_cast<float2*>(B), kb, N);
+        ring_smem_attr(ts_update32_kernel, RU_SMEM, g_update_attr);
+        const int bca = std::min(RU_COLS, ka);
+        const CUtensorMap tmA = column_map(A, N, ka, bca);
+        ts_update32_kernel<<<(unsigned)((N + RU_ROWS - 1) / RU_ROWS), RU_THREADS, RU_SMEM, st>>>(
+            tmA, ka, bca, coef, reinterpret_cast<float2*>(B), kb, N, err);
     } else if (kb <= 8) {
         ts_update_kernel<V, 8><<<nblocks(N), 256, 0, st>>>(A, ka, H, alpha, B, kb, N);
     } else {
@@ -957,13 +1202,13 @@ void launch_ts_trsm(V* B, int kb, int64_t N, const double2* R, cudaStream_t st) 
 }
 
 template void launch_ts_gram<float2>(const float2*, int, const float2*, int, int64_t, double2*,
-                                     double2*, int, cudaStream_t);
+                                     double2*, int, cudaStream_t, int*);
 template void launch_ts_gram<double2>(const double2*, int, const double2*, int, int64_t, double2*,
-                                      double2*, int, cudaStream_t);
+                                      double2*, int, cudaStream_t, int*);
 template void launch_ts_update<float2>(const float2*, int, const double2*, double, float2*, int,
-                                       int64_t, cudaStream_t, float2*);
+                                       int64_t, cudaStream_t, float2*, int*);
 template void launch_ts_update<double2>(const double2*, int, const double2*, double, double2*, int,
-                                        int64_t, cudaStream_t, float2*);
+                                        int64_t, cudaStream_t, float2*, int*);
 template void launch_ts_trsm<float2>(float2*, int, int64_t, const double2*, cudaStream_t);
 template void launch_ts_trsm<double2>(double2*, int, int64_t, const double2*, cudaStream_t);
 

@@ -826,7 +826,7 @@ void cholqr2_dev(mbs_ctx* c, V* W, int64_t N, int s, double2* Bs, double2* d_gra
     double* ok = reinterpret_cast<double*>(Bs + 2 * s * s);
     for (int pass = 0; pass < 2; ++pass) {
         double2* R = Bs + (size_t)pass * s * s;
-        launch_ts_gram<V>(W, s, W, s, N, d_gram, d_part, nb, c->st);
+        launch_ts_gram<V>(W, s, W, s, N, d_gram, d_part, nb, c->st, device_err(c));
         launch_chol_small(d_gram, s, R, ok + pass, c->st);
         launch_ts_trsm<V>(W, s, N, R, c->st);
     }
@@ -1004,8 +1004,9 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             double2* h2 = h1 + (size_t)K * s;
             for (int pass = 0; pass < 2; ++pass) {
                 double2* hp = pass == 0 ? h1 : h2;
-                launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s, f32), c->st);
-                launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st, d_coef);
+                launch_ts_gram<V>(basis, K, w, s, N, hp, d_part, ts_gram_blocks(N, K, s, f32), c->st,
+                                  device_err(c));
+                launch_ts_update<V>(basis, K, hp, -1.0, w, s, N, c->st, d_coef, device_err(c));
             }
             V* vn = basis + (size_t)(j + 1) * NV;
             MBS_CUDA_TRY(cudaMemcpyAsync(vn, w, NV * sizeof(V), cudaMemcpyDeviceToDevice, c->st));
@@ -1101,7 +1102,7 @@ GmresStats bgmres(mbs_ctx* c, int s, const V* b, V* x, bool x_zero, double tol, 
             double2* d_y = scratch<double2>(c, "bg_y", (size_t)restart * s * s);
             std::vector<double2> stage;
             from_host_cd(Y, d_y, c->st, stage);
-            launch_ts_update<V>(basis, Mj, d_y, 1.0, x, s, N, c->st, d_coef);
+            launch_ts_update<V>(basis, Mj, d_y, 1.0, x, s, N, c->st, d_coef, device_err(c));
         }
         bool est_conv = true;
         for (int q = 0; q < s; ++q) est_conv = est_conv && S.relres[q] <= tol;
@@ -1169,7 +1170,7 @@ mbs_status guarded(mbs_ctx* c, F&& f) {
             MBS_CUDA_TRY(cudaStreamSynchronize(c->st));
             if (e) {
                 MBS_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
-                throw MbsError{MBS_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core G_hat kernel)"};
+                throw MbsError{MBS_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core G_hat or block Gram-Schmidt kernel)"};
             }
         }
         if (s == MBS_OK) c->err.clear();

@@ -205,12 +205,15 @@ int ts_gram_blocks(int64_t N, int ka, int kb, bool f32);
 // Cholesky G = R^H R of an s x s Hermitian matrix on the device (s <= 16);
 // *ok = 1, or 0 (and R = I) if G is not numerically positive definite.
 void launch_chol_small(const double2* G, int s, double2* R, double* ok, cudaStream_t st);
+// The FP32 kernels stream the basis through shared memory with bounded waits
+// and need err, the context's device error flag (set if a wait ran out; the
+// outputs are then NaN).
 template <typename V>
 void launch_ts_gram(const V* A, int ka, const V* B, int kb, int64_t N, double2* C,
-                    double2* scratch, int nblk, cudaStream_t st);
+                    double2* scratch, int nblk, cudaStream_t st, int* err);
 template <typename V>
 void launch_ts_update(const V* A, int ka, const double2* H, double alpha, V* B, int kb, int64_t N,
-                      cudaStream_t st, float2* coef = nullptr);
+                      cudaStream_t st, float2* coef = nullptr, int* err = nullptr);
 template <typename V>
 void launch_ts_trsm(V* B, int kb, int64_t N, const double2* R, cudaStream_t st);
 void launch_f64_to_f32(const double2* a, float2* b, int64_t n, cudaStream_t st);
