@@ -109,6 +109,9 @@ def parse():
                          "(for profiling the dominant kernel); prints per-launch times")
     ap.add_argument("--bodies", type=int, default=0,
                     help="with --kernel: the first B bodies of the workload only (small profiling case)")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="build S and run one solve of the workload with the bench's solver options "
+                         "(for profiling the Krylov kernels); prints its time and counts, not a bench line")
     return ap.parse_args()
 
 
@@ -199,6 +202,34 @@ def run_serving(a, pkg, mi):
     out["p50_s"], out["p99_s"] = full["p50_s"], full["p99_s"]
     out["overlap_fraction"] = full["overlap_fraction"]
     return out
+
+
+def run_solve_only(a):
+    import numpy as np
+    import torch
+
+    import mbs_inputs as mi
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_19113_gb300 as pkg
+
+    wl = {1: mi.config1, 2: mi.config2, 3: mi.config3}[a.config]()
+    stream = torch.cuda.current_stream()
+    ctx = pkg.Context(wl.dim, wl.kappa, precision=pkg.PREC_MIXED, tol=a.tol, inner_tol=a.inner_tol,
+                      restart=a.restart, fp64_kernel=a.fp64_kernel, max_iter=50000, max_sweeps=12,
+                      stream=stream.cuda_stream, mac_path=a.mac)
+    ctx.build_scattering_matrices(wl)
+    v = torch.from_numpy(np.ascontiguousarray(wl.boundary_data().T)).cuda().T
+    b = ctx.rhs(v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info = ctx.solve(b)
+    torch.cuda.synchronize()
+    out = {"solve_only": True, "config": a.config, "restart": a.restart, "tol": a.tol,
+           "solve_s": time.perf_counter() - t0}
+    out.update(info)
+    print(json.dumps(out), flush=True)
+    ctx.close()
 
 
 def run_kernel_only(a):
@@ -654,6 +685,8 @@ def main():
     ws, rank, local = dist_setup()
     if a.kernel:
         run_kernel_only(a)
+    elif a.solve_only:
+        run_solve_only(a)
     elif a.impl == "reference":
         run_reference(a, ws, rank)
     else:
