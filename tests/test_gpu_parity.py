@@ -285,6 +285,24 @@ def test_injected_solve_fp64_and_mixed_config0(pkg):
         assert _rel(u, u_ref) < tol
 
 
+@pytest.mark.parametrize("nrhs", [1, 2, 5, 8])
+def test_mixed_solve_through_the_fp32_gram_schmidt_rings(pkg, nrhs):
+    """Mixed solves whose FP32 block Gram-Schmidt runs on the tensor-copy ring
+    kernels (even N, block width <= 8) at the shapes their boxes cut: N not a
+    multiple of the 64-row stage, block widths 1-8, basis widths of 6 to 48
+    columns (restart 6: below and across the 16- and 32-column boxes) and up
+    to 320 (restart 40), against the oracle's dense solve with the same S."""
+    wl = mi.tiny_2d(seed=2, T=9, kappa=6.0, nrhs=nrhs, ks=(24, 38, 50))
+    ref = orc.solve_workload(wl)
+    for restart in (6, 40):
+        ctx, sdata, lay = _ctx_with_oracle_S(pkg, wl, precision=pkg.PREC_MIXED, tol=1e-12, restart=restart)
+        assert ctx.N % 2 == 0 and ctx.N % 64 != 0
+        q, info = ctx.solve(ref["b"])
+        assert info["converged"] == 1
+        assert _nrel(q, ref["q"]) < 1e-9
+        ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_block_gmres_graph_replay_matches_direct(pkg, prec):
     """Block GMRES steps replayed from captured CUDA graphs give bitwise the
