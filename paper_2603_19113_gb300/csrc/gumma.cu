@@ -39,6 +39,7 @@
 // with per-target, per-body constants, then r, r - R = s / (r + R), the fitted
 // modulus/phase of H0 and exp(i phase); near body pairs take the per-pair
 // branches of pair_phi_f32.
+#include "bulk.cuh"
 #include "phi32.cuh"
 
 namespace {
@@ -71,34 +72,8 @@ __device__ __forceinline__ int b_word(int n, int k) {
     return ((k >> 2) * (NM / 8) + (n >> 3)) * 32 + (n & 7) * 4 + (k & 3);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // Wait for the phase of the given parity; false after UM_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try(bar, parity))
-        if (global_ns() - t0 > UM_WAIT_NS) return false;
-    return true;
-}
+__device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t parity) { return mbar_wait(bar, parity, UM_WAIT_NS); }
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -125,12 +100,8 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
                                           uint32_t bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
+    mbar_arrive_expect(bar, bytes);
+    bulk_copy(dst, src, bytes, bar);
 }
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
@@ -310,10 +281,10 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
     const uint32_t b_afull = smem_u32(&bar_afull), b_mdone = smem_u32(&bar_mdone);
     if (tid == 0) {
         for (int st = 0; st < UM_STAGES; ++st)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[st])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(b_afull));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_mdone));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            mbar_init(smem_u32(&bar_full[st]), 1);
+        mbar_init(b_afull, 4);
+        mbar_init(b_mdone, 1);
+        mbar_init_fence();
         s_abort = 0;
     }
     if (warp == 0) {
@@ -351,7 +322,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                     ++sig;
                     first = true;
                 }
-                if (!mbar_wait(b_afull, (uint32_t)(g & 1)) || s_abort) {
+                if (!um_wait(b_afull, (uint32_t)(g & 1)) || s_abort) {
                     ok = false;
                     break;
                 }
@@ -371,7 +342,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                 first = false;
                 if (issued < G) {
                     // this chunk's stage is refilled once its MMAs are done
-                    if (!mbar_wait(b_mdone, (uint32_t)(g & 1))) {
+                    if (!um_wait(b_mdone, (uint32_t)(g & 1))) {
                         ok = false;
                         ++g;
                         break;
@@ -383,10 +354,10 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
             }
             if (!ok) {
                 s_abort = 1;
-                if (g > 0) mbar_wait(b_mdone, (uint32_t)((g - 1) & 1));  // bounded drain
+                if (g > 0) um_wait(b_mdone, (uint32_t)((g - 1) & 1));  // bounded drain
             }
             for (int gg = g; gg < issued; ++gg)
-                mbar_wait(smem_u32(&bar_full[gg % UM_STAGES]), (uint32_t)((gg / UM_STAGES) & 1));
+                um_wait(smem_u32(&bar_full[gg % UM_STAGES]), (uint32_t)((gg / UM_STAGES) & 1));
         }
         __syncwarp();
     } else {
@@ -465,7 +436,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
             const float glast = (wvfar ? c_f32_64G[MBS_F32_X64_DEG] : c_f32_8G[MBS_F32_X8_DEG]) + phi0;
 
             for (int c = cb; c < ce; ++c, ++g) {
-                if (!mbar_wait(smem_u32(&bar_full[stage]), fphase)) s_abort = 1;
+                if (!um_wait(smem_u32(&bar_full[stage]), fphase)) s_abort = 1;
                 const float4* src = reinterpret_cast<const float4*>(um_smem + stage * C::REC + 2 * C::TILE);
                 const int cnt = c == ce - 1 ? klast : UM_KC;  // staged sources of this chunk
                 // the fast path also takes a body's ragged last chunk: its padding
@@ -527,7 +498,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                     if (half == 0 && g > 0) {
                         // the previous chunk's MMAs are done: A is free, and a body
                         // that ended with that chunk has its D complete
-                        if (!mbar_wait(b_mdone, (uint32_t)((g - 1) & 1))) s_abort = 1;
+                        if (!um_wait(b_mdone, (uint32_t)((g - 1) & 1))) s_abort = 1;
                         tc_fence_after();
                         if (pending) {
                             read_d();
@@ -541,7 +512,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0)
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_afull) : "memory");
+                    mbar_arrive(b_afull);
                 pending = c == ce - 1;
                 stage = stage + 1 == UM_STAGES ? 0 : stage + 1;
                 fphase ^= stage == 0 ? 1u : 0u;
@@ -554,7 +525,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) g_umma_kernel(const GLayout L, 
         }
         if (!abort && G > 0) {
             // the MMAs of the last chunk have not been waited for yet
-            if (!mbar_wait(b_mdone, (uint32_t)((G - 1) & 1))) abort = true;
+            if (!um_wait(b_mdone, (uint32_t)((G - 1) & 1))) abort = true;
             tc_fence_after();
             abort = __any_sync(0xffffffffu, abort);
             if (!abort && pending) read_d();
